@@ -1,0 +1,146 @@
+"""Whole-netlist pins of the oracle.
+
+- The global event-driven simulator and the levelized Algorithm 2 evaluator
+  are independent code and must agree exactly (processing order is
+  irrelevant for a DAG, Sec. 4.1).
+- Settle values: the last value of every waveform equals a static 4-value
+  evaluation with the final primary-input values.
+- Invariants: strictly increasing times, no repeated consecutive values, the
+  first value is never X, and Eq. 2: |out| <= distinct fanin timestamps
+  <= sum of fanin lengths.
+- Closed form: a chain of BUF/INV cells with rise = fall = d shifts the
+  input by k*d, reads Z as X, inverts for odd INV count and drops repeats.
+- A cyclic netlist is rejected.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+X, Z = 2, 3
+
+
+def small_cases():
+    cases = []
+    for seed in range(1, 41):
+        rng = np.random.default_rng(seed)
+        n_pi = int(rng.integers(1, 6))
+        depth = int(rng.integers(1, 7))
+        G = int(rng.integers(depth, 40))
+        mask = int(rng.integers(1, synth.ALL_CELLS + 1))
+        nl = synth.make_netlist(n_pi, G, depth, fanout="geometric" if seed % 2 else "pareto",
+                                d_min=1, d_max=int(rng.integers(1, 30)), cells=mask, seed=seed,
+                                shuffle=bool(seed % 3 == 0))
+        st = synth.make_stimulus(n_pi, mean=float(rng.integers(1, 40)), window=int(rng.integers(20, 400)),
+                                 probs=(0.4, 0.4, 0.1, 0.1), seed=seed)
+        cases.append((nl, st))
+    return cases
+
+
+def test_event_driven_equals_levelized():
+    for nl, st in small_cases() + [(w.netlist, w.stimulus) for w in [synth.make_workload("tiny200", seed=s) for s in (1, 2, 3)]]:
+        a = oracle.sim_event(nl, st)
+        b = oracle.sim_levelized(nl, st, nthreads=2)
+        assert np.array_equal(a.off, b.off)
+        assert np.array_equal(a.t, b.t)
+        assert np.array_equal(a.v, b.v)
+
+
+def test_settle_values_equal_static_eval():
+    for nl, st in small_cases():
+        r = oracle.sim_levelized(nl, st)
+        lens = np.diff(st.off)
+        pi_final = np.where(lens > 0, st.v[np.maximum(st.off[1:] - 1, 0)], X).astype(np.uint8)
+        want = oracle.static_eval(nl, pi_final)
+        lens_r = np.diff(r.off)
+        got = np.where(lens_r > 0, r.v[np.maximum(r.off[1:] - 1, 0)], X)
+        assert np.array_equal(got, want)
+
+
+def test_invariants_and_eq2_bound():
+    for nl, st in small_cases():
+        r = oracle.sim_levelized(nl, st)
+        for n in range(nl.n_nets):
+            t, v = r.net(n)
+            assert np.all(np.diff(t) > 0)
+            assert np.all(v[1:] != v[:-1])
+            if n >= nl.n_pi and len(v):
+                assert v[0] != X
+                assert np.all(v != Z)
+        for g in range(nl.n_gates):
+            fins = nl.fanin_net[nl.fanin_off[g]:nl.fanin_off[g + 1]]
+            ts = [r.net(int(f))[0] for f in fins]
+            distinct = len(np.unique(np.concatenate(ts))) if ts else 0
+            out = len(r.net(nl.n_pi + g)[0])
+            assert out <= distinct <= sum(len(t) for t in ts)
+
+
+def _chain(cells, d):
+    from synth import Netlist
+    G = len(cells)
+    typ = np.array(cells, np.uint8)
+    off = np.arange(G + 1, dtype=np.int32)
+    net = np.arange(G, dtype=np.int32)     # gate g reads net g (PI 0, then gate g-1)
+    dd = np.full(G, d, np.int32)
+    return Netlist(1, typ, off, net, dd, dd.copy())
+
+
+def test_buf_inv_chain_closed_form():
+    rng = np.random.default_rng(3)
+    for trial in range(50):
+        cells = rng.choice([oracle.INV, oracle.BUF], size=int(rng.integers(1, 8))).tolist()
+        d = int(rng.integers(1, 20))
+        nl = _chain(cells, d)
+        n = int(rng.integers(0, 30))
+        ts = np.sort(rng.choice(np.arange(0, 500), size=n, replace=False)).astype(np.int32)
+        vs, prev = [], X
+        for _ in range(n):
+            v = int(rng.choice([x for x in (0, 1, X, Z) if x != prev]))
+            vs.append(v)
+            prev = v
+        st = synth.Stimulus(np.array([0, n], np.int64), ts, np.array(vs, np.uint8))
+        r = oracle.sim_levelized(nl, st)
+        k = len(cells)
+        inv = sum(c == oracle.INV for c in cells) % 2
+        want, prev = [], X
+        for t, v in zip(ts.tolist(), vs):
+            v = X if v == Z else v
+            if inv and v != X:
+                v = 1 - v
+            if v != prev:
+                want.append((t + k * d, v))
+                prev = v
+        t, v = r.net(k)
+        assert list(zip(t.tolist(), v.tolist())) == want
+
+
+def test_cycle_rejected():
+    from synth import Netlist
+    # gate 0 reads gate 1, gate 1 reads gate 0
+    nl = Netlist(1, np.array([oracle.AND2, oracle.BUF], np.uint8), np.array([0, 2, 3], np.int32),
+                 np.array([0, 2, 1], np.int32), np.ones(3, np.int32), np.ones(3, np.int32))
+    st = synth.Stimulus(np.array([0, 1], np.int64), np.array([5], np.int32), np.array([1], np.uint8))
+    with pytest.raises(oracle.OracleError):
+        oracle.sim_levelized(nl, st)
+    with pytest.raises(oracle.OracleError):
+        oracle.sim_event(nl, st)
+
+
+def test_check_gates_detects_planted_mistakes():
+    w = synth.make_workload("tiny200", seed=5)
+    nl, st = w.netlist, w.stimulus
+    r = oracle.sim_levelized(nl, st)
+    t32 = r.t.astype(np.int32)
+    assert oracle.check_gates(nl, r.off, t32, r.v) == (0, -1)
+    # shift one output transition of a gate with events: exactly that gate (and
+    # its readers) stop matching
+    lens = np.diff(r.off)
+    g = int(np.nonzero(lens[nl.n_pi:] > 2)[0][0])
+    e = int(r.off[nl.n_pi + g] + 1)
+    t_bad = t32.copy()
+    t_bad[e] += 1 if t_bad[e] + 1 < t_bad[e + 1] else 0
+    v_bad = r.v.copy()
+    v_bad[e] = 1 - v_bad[e] if v_bad[e] in (0, 1) else 0
+    bad, first = oracle.check_gates(nl, r.off, t_bad, v_bad)
+    assert bad >= 1 and first <= g
