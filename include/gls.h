@@ -1,0 +1,203 @@
+/*
+ * gls.h -- C-ABI of libgls.so: timing-aware 4-value gate-level re-simulation
+ * on one GB300 GPU (sm_103a), the data-parallel hot path of arXiv 2304.13398
+ * ("Acceleration for Timing-Aware Gate-Level Logic Simulation with One-Pass
+ * GPU Parallelism").
+ *
+ * Problem (Sec. 2.1): given a combinational netlist of library cells, their
+ * 4-value functions (Sec. 2.2, Table 1) and pin-to-pin delays (Sec. 2.3), and
+ * the waveforms of the primary inputs over a duration, compute the waveform of
+ * every other net.  A waveform is a strictly time-ordered list of transitions
+ * (time in ps, value in {0, 1, X, Z}); a net is X before its first transition.
+ *
+ * Semantics of one gate (Algorithm 2, Eq. 1): the fanin waveforms are merged
+ * by time and all transitions at one time are applied together; when the cell
+ * value changes, a transition is scheduled at t + min over the pins with a
+ * transition at t of that pin's delay toward the new value (rise for 1, fall
+ * for 0, the smaller of both for X); a new scheduled transition denies every
+ * earlier-determined one that would appear at the same time or later, and a
+ * transition equal to the value before it is dropped.  Z is read as X on
+ * inputs; cells never output Z.
+ *
+ * Conventions for every call:
+ *   - Return value: GLS_OK (0) or a negative gls_status; no exception, abort
+ *     or signal crosses this boundary.  gls_last_error() describes the last
+ *     failure on the calling thread.
+ *   - Ownership: arrays passed in are read during the call only (the library
+ *     copies what it keeps); all device memory is owned by the context and
+ *     freed by gls_release / gls_destroy.  Output arrays are caller-owned.
+ *   - Pointers are host pointers unless a parameter says "device".
+ *   - Net ids: 0..n_pi-1 are the primary inputs, n_pi+g is the output of
+ *     gate g (in the caller's gate order).
+ *   - Times are int32 ps; every time that can occur in a run (input times plus
+ *     the largest path delay) must stay below 2^30 (else GLS_ERANGE), because
+ *     the device stores a transition as one 32-bit word (time << 2 | value).
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef GLS_H
+#define GLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gls_ctx gls_ctx;
+
+typedef enum gls_status {
+    GLS_OK = 0,
+    GLS_EINVAL = -1,     /* bad argument, unknown id, malformed netlist            */
+    GLS_ECYCLE = -2,     /* the netlist is not a DAG                               */
+    GLS_ESTIM = -3,      /* malformed stimulus (order, value range, repeats)       */
+    GLS_ERANGE = -4,     /* a time would reach 2^30, or a cell's delay spread is    */
+                         /* beyond the device limit GLS_MAX_DELAY_SPREAD            */
+    GLS_ENOMEM = -5,     /* device or host allocation failed / budget exceeded     */
+    GLS_EOVERFLOW = -6,  /* output larger than the given capacity or run arena     */
+    GLS_ETIMEOUT = -7,   /* a bounded device wait gave up                          */
+    GLS_ECUDA = -8       /* CUDA runtime error                                     */
+} gls_status;
+
+/* Cell library (Sec. 2.1 "cells derived from basic gates"); pins a, b, c. */
+typedef enum gls_cell {
+    GLS_INV = 0,   /* !a             */
+    GLS_BUF,       /* a              */
+    GLS_AND2,      /* a & b          */
+    GLS_OR2,       /* a | b          */
+    GLS_NAND2,     /* !(a & b)       */
+    GLS_NOR2,      /* !(a | b)       */
+    GLS_XOR2,      /* a ^ b          */
+    GLS_XNOR2,     /* !(a ^ b)       */
+    GLS_MUX2,      /* c ? b : a      */
+    GLS_AOI21,     /* !((a & b) | c) */
+    GLS_OAI21,     /* !((a | b) & c) */
+    GLS_NCELLS
+} gls_cell;
+
+/* Largest (max - min) over one cell's rise/fall delays that the device
+   pending-transition buffer supports; larger spreads give GLS_ERANGE. */
+#define GLS_MAX_DELAY_SPREAD 255
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int gls_version(void);
+
+/* Pin count of a cell, or GLS_EINVAL. */
+int gls_cell_arity(int cell);
+
+/*
+ * Host-only validation and levelization of a netlist (no GPU needed).
+ *   type[n_gates], fanin_off[n_gates+1] (fanin_off[0] = 0), fanin_net[A],
+ *   d_rise[A], d_fall[A] with A = fanin_off[n_gates]: gate g reads nets
+ *   fanin_net[fanin_off[g] .. fanin_off[g+1]) as pins a, b, c; arc delays in
+ *   ps, each in [1, 2^29).
+ * Checks: pin count matches the cell, net ids in range, delays in range,
+ * delay spread per cell <= GLS_MAX_DELAY_SPREAD (GLS_ERANGE), no cycle
+ * (GLS_ECYCLE).  On success *depth_out is the longest path in gates and, when
+ * level_out is non-NULL, level_out[g] is gate g's level (1 + max fanin level,
+ * primary inputs at level 0).
+ */
+int gls_check_netlist(int32_t n_pi, int32_t n_gates, const uint8_t *type, const int32_t *fanin_off,
+                      const int32_t *fanin_net, const int32_t *d_rise, const int32_t *d_fall,
+                      int32_t *depth_out, int32_t *level_out);
+
+/*
+ * Host-only validation of a stimulus (the given waveforms, Sec. 2.1).
+ *   off[n_pi+1] int64 with off[0] = 0 and non-decreasing; PI i owns
+ *   transitions [off[i], off[i+1]) of t (int32 ps) and v (0, 1, 2 = X, 3 = Z).
+ * Rules: 0 <= t < 2^30 strictly increasing per PI, v <= 3, no value equal to
+ * the one before it in the same PI.  Returns GLS_OK or GLS_ESTIM.
+ */
+int gls_check_stimulus(int32_t n_pi, const int64_t *off, const int32_t *t, const uint8_t *v);
+
+/*
+ * Create a context on CUDA device 'device'.  hbm_budget_bytes caps the device
+ * memory the context may hold (0 = 90% of the free memory at creation).
+ */
+int gls_create(gls_ctx **out, int device, uint64_t hbm_budget_bytes);
+
+/* Free every object of the context and the context itself (NULL is a no-op). */
+void gls_destroy(gls_ctx *ctx);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *gls_last_error(gls_ctx *ctx);
+
+/*
+ * Validate (as gls_check_netlist), levelize and copy a netlist to the device:
+ * gates are reordered by level into a structure-of-arrays record per gate;
+ * the device copy is immutable.  *netlist_id receives a handle.
+ */
+int gls_load_netlist(gls_ctx *ctx, int32_t n_pi, int32_t n_gates, const uint8_t *type,
+                     const int32_t *fanin_off, const int32_t *fanin_net, const int32_t *d_rise,
+                     const int32_t *d_fall, int32_t *netlist_id);
+
+/*
+ * Copy primary-input waveforms (layout of gls_check_stimulus) to the device
+ * in one host-to-device transfer, validate them there and pack each
+ * transition into one 32-bit word.  Synchronous.  GLS_ESTIM on a rule
+ * violation.  *stim_id receives a handle usable with any netlist of the same
+ * n_pi.
+ */
+int gls_load_stimulus(gls_ctx *ctx, int32_t n_pi, const int64_t *off, const int32_t *t,
+                      const uint8_t *v, int32_t *stim_id);
+
+/*
+ * Overwrite an existing stimulus in place with new waveforms of the same n_pi
+ * and at most the event count it was created with (GLS_EOVERFLOW otherwise).
+ * Runs created on it see the new waveforms at their next gls_rerun.
+ * Synchronous like gls_load_stimulus.
+ */
+int gls_update_stimulus(gls_ctx *ctx, int32_t stim_id, const int64_t *off, const int32_t *t,
+                        const uint8_t *v);
+
+/*
+ * Simulate a netlist under a stimulus: allocate the run's waveform store
+ * (net descriptors plus an event arena of arena_events 32-bit words; 0 means
+ * 256 words per stimulus transition plus 2^20, capped at half of the unused
+ * budget) and enqueue the whole level-by-level evaluation as one
+ * CUDA graph on cuda_stream (a cudaStream_t; NULL = the context's stream).
+ * Stream-ordered: returns once the work is enqueued.  The result stays on the
+ * device until gls_release.  GLS_ERANGE if a time could reach 2^30.
+ */
+int gls_simulate(gls_ctx *ctx, int32_t netlist_id, int32_t stim_id, int64_t arena_events,
+                 void *cuda_stream, int32_t *run_id);
+
+/* Enqueue the same run again (same buffers, current stimulus contents). */
+int gls_rerun(gls_ctx *ctx, int32_t run_id, void *cuda_stream);
+
+/*
+ * Wait for a run and report it: *total_events = output transitions of all
+ * gates, *kernel_ms = device time of the last enqueued evaluation (CUDA
+ * events around the level sequence).  Either pointer may be NULL.
+ * GLS_EOVERFLOW when the event arena was too small: then *total_events is the
+ * arena demand of the gates that were evaluated, a lower bound of the full
+ * demand because gates that did not fit leave their readers fewer inputs
+ * (retry with at least that much), GLS_ERANGE when a cell's pending transitions
+ * exceeded the device buffer.
+ */
+int gls_run_stats(gls_ctx *ctx, int32_t run_id, int64_t *total_events, double *kernel_ms);
+
+/*
+ * Copy one net's waveform to the host: times into t[cap], values into
+ * v[cap].  *n_out always receives the length; GLS_EOVERFLOW if cap < length
+ * (nothing copied).  Synchronises with the run.
+ */
+int gls_read_waveform(gls_ctx *ctx, int32_t run_id, int32_t net, int32_t *t, uint8_t *v,
+                      int64_t cap, int64_t *n_out);
+
+/*
+ * Copy every net's waveform to the host as one CSR: off[n_nets+1] (int64,
+ * caller-allocated) and packed[cap] transitions, each (time << 2) | value,
+ * nets in id order.  The device gathers the store into net order first so the
+ * result comes back in a single device-to-host transfer.  GLS_EOVERFLOW if
+ * cap is smaller than the total (off is still filled).  Synchronous.
+ */
+int gls_read_all(gls_ctx *ctx, int32_t run_id, int64_t *off, uint32_t *packed, int64_t cap);
+
+/* Free a netlist, stimulus or run handle (ids are unique per context). */
+int gls_release(gls_ctx *ctx, int32_t id);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLS_H */

@@ -1,0 +1,740 @@
+// gls_api.cu -- host side of libgls.so: validation, levelization, device
+// layout, run graphs and read-back.  Every entry point declared in gls.h is
+// defined here; no exception crosses the C boundary.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gls_internal.h"
+#include "../../include/gls.h"
+
+using namespace gls;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(GLS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int kArity[GLS_NCELLS] = {1, 1, 2, 2, 2, 2, 2, 2, 3, 3, 3};
+constexpr int32_t kMaxDelay = 1 << 29;
+
+// ---- 4-value cell tables -------------------------------------------------
+// Each cell is written as the disjunction of all its prime implicants; Kleene
+// evaluation of that cover (AND: 0 if a literal is 0, 1 if all are 1, else X;
+// OR: 1 if a term is 1, 0 if all are 0, else X) gives 1 exactly when every
+// 0/1 completion of the unknown inputs gives 1, and 0 exactly when every
+// completion gives 0 -- the reading of X as "either 0 or 1" of Sec. 2.2.
+// Literal per pin: +1 the pin, -1 its complement, 0 absent.
+struct Cover { int nterms; int8_t lit[3][3]; };
+const Cover kCovers[GLS_NCELLS] = {
+    {1, {{-1, 0, 0}}},                              // INV   !a
+    {1, {{+1, 0, 0}}},                              // BUF   a
+    {1, {{+1, +1, 0}}},                             // AND2  ab
+    {2, {{+1, 0, 0}, {0, +1, 0}}},                  // OR2   a + b
+    {2, {{-1, 0, 0}, {0, -1, 0}}},                  // NAND2 !a + !b
+    {1, {{-1, -1, 0}}},                             // NOR2  !a!b
+    {2, {{+1, -1, 0}, {-1, +1, 0}}},                // XOR2  a!b + !ab
+    {2, {{+1, +1, 0}, {-1, -1, 0}}},                // XNOR2 ab + !a!b
+    {3, {{+1, 0, -1}, {0, +1, +1}, {+1, +1, 0}}},   // MUX2  a!c + bc + ab
+    {2, {{-1, 0, -1}, {0, -1, -1}}},                // AOI21 !a!c + !b!c
+    {2, {{-1, -1, 0}, {0, 0, -1}}},                 // OAI21 !a!b + !c
+};
+
+int kleene_cover(const Cover &c, const int in[3]) {
+    int any_x = 0;
+    for (int t = 0; t < c.nterms; t++) {
+        int term = 1;  // 1, 0 or 2 (X)
+        for (int p = 0; p < 3; p++) {
+            if (!c.lit[t][p]) continue;
+            int v = in[p];                         // 0, 1 or 2
+            if (v != 2 && c.lit[t][p] < 0) v = 1 - v;
+            if (v == 0) { term = 0; break; }
+            if (v == 2) term = 2;
+        }
+        if (term == 1) return 1;
+        if (term == 2) any_x = 1;
+    }
+    return any_x ? 2 : 0;
+}
+
+void build_luts(uint64_t lut[GLS_NCELLS][2]) {
+    for (int c = 0; c < GLS_NCELLS; c++) {
+        lut[c][0] = lut[c][1] = 0;
+        for (int idx = 0; idx < 64; idx++) {
+            int in[3];
+            for (int p = 0; p < 3; p++) {
+                int v = (idx >> (2 * p)) & 3;
+                in[p] = v == 3 ? 2 : v;            // Z is read as X
+            }
+            uint64_t f = (uint64_t)kleene_cover(kCovers[c], in);
+            lut[c][idx >> 5] |= f << (2 * (idx & 31));
+        }
+    }
+}
+
+// ---- host netlist analysis ------------------------------------------------
+struct Levelized {
+    int32_t depth = 0;
+    std::vector<int32_t> level;        // per external gate
+    std::vector<int32_t> order;        // internal position -> external gate
+    std::vector<int32_t> pos;          // external gate -> internal position
+    std::vector<int32_t> level_begin;  // [depth+2], gates of level L at [level_begin[L], level_begin[L+1])
+    int64_t max_path_delay = 0;
+};
+
+int analyse_netlist(int32_t n_pi, int32_t G, const uint8_t *type, const int32_t *fanin_off, const int32_t *fanin_net,
+                    const int32_t *d_rise, const int32_t *d_fall, Levelized *out) {
+    if (n_pi < 0 || G < 0) return fail(GLS_EINVAL, "negative n_pi or n_gates");
+    if (G > 0 && (!type || !fanin_off || !fanin_net || !d_rise || !d_fall))
+        return fail(GLS_EINVAL, "NULL netlist array");
+    if ((int64_t)n_pi + G >= (int64_t)INT32_MAX) return fail(GLS_EINVAL, "too many nets");
+    const int64_t N = (int64_t)n_pi + G;
+    if (G > 0 && fanin_off[0] != 0) return fail(GLS_EINVAL, "fanin_off[0] must be 0");
+    for (int32_t g = 0; g < G; g++) {
+        if (type[g] >= GLS_NCELLS) return fail(GLS_EINVAL, "gate %d: unknown cell %d", g, type[g]);
+        if (fanin_off[g + 1] - fanin_off[g] != kArity[type[g]])
+            return fail(GLS_EINVAL, "gate %d: %d fanins for a %d-pin cell", g, fanin_off[g + 1] - fanin_off[g],
+                        kArity[type[g]]);
+        int32_t lo = INT32_MAX, hi = 0;
+        for (int32_t a = fanin_off[g]; a < fanin_off[g + 1]; a++) {
+            if (fanin_net[a] < 0 || fanin_net[a] >= N) return fail(GLS_EINVAL, "gate %d: net %d out of range", g, fanin_net[a]);
+            if (fanin_net[a] == n_pi + g) return fail(GLS_ECYCLE, "gate %d reads its own output", g);
+            if (d_rise[a] < 1 || d_fall[a] < 1 || d_rise[a] >= kMaxDelay || d_fall[a] >= kMaxDelay)
+                return fail(GLS_EINVAL, "gate %d: delay out of [1, 2^29)", g);
+            lo = std::min(lo, std::min(d_rise[a], d_fall[a]));
+            hi = std::max(hi, std::max(d_rise[a], d_fall[a]));
+        }
+        if (hi - lo > GLS_MAX_DELAY_SPREAD)
+            return fail(GLS_ERANGE, "gate %d: delay spread %d exceeds %d", g, hi - lo, GLS_MAX_DELAY_SPREAD);
+    }
+    // Kahn's algorithm over gate->gate arcs; level = 1 + max fanin level
+    std::vector<int32_t> need(G, 0), level(G, 1), fo_cnt(G + 1, 0);
+    for (int32_t g = 0; g < G; g++)
+        for (int32_t a = fanin_off[g]; a < fanin_off[g + 1]; a++)
+            if (fanin_net[a] >= n_pi) { need[g]++; fo_cnt[fanin_net[a] - n_pi + 1]++; }
+    for (int32_t g = 0; g < G; g++) fo_cnt[g + 1] += fo_cnt[g];
+    std::vector<int32_t> fo(fo_cnt[G]), fill(fo_cnt.begin(), fo_cnt.end() - 1);
+    for (int32_t g = 0; g < G; g++)
+        for (int32_t a = fanin_off[g]; a < fanin_off[g + 1]; a++)
+            if (fanin_net[a] >= n_pi) fo[fill[fanin_net[a] - n_pi]++] = g;
+    std::vector<int32_t> queue;
+    queue.reserve(G);
+    for (int32_t g = 0; g < G; g++) if (need[g] == 0) queue.push_back(g);
+    for (size_t h = 0; h < queue.size(); h++) {
+        int32_t g = queue[h];
+        for (int32_t s = fo_cnt[g]; s < fo_cnt[g + 1]; s++) {
+            int32_t x = fo[s];
+            level[x] = std::max(level[x], level[g] + 1);
+            if (--need[x] == 0) queue.push_back(x);
+        }
+    }
+    if ((int64_t)queue.size() != G) return fail(GLS_ECYCLE, "netlist has a cycle (%lld gates on or behind it)",
+                                                (long long)(G - (int64_t)queue.size()));
+    if (!out) return GLS_OK;
+    out->depth = 0;
+    for (int32_t g = 0; g < G; g++) out->depth = std::max(out->depth, level[g]);
+    out->level_begin.assign(out->depth + 2, 0);
+    for (int32_t g = 0; g < G; g++) out->level_begin[level[g] + 1]++;
+    for (int32_t L = 0; L <= out->depth; L++) out->level_begin[L + 1] += out->level_begin[L];
+    out->order.resize(G);
+    out->pos.resize(G);
+    std::vector<int32_t> f2(out->level_begin.begin(), out->level_begin.end());
+    for (int32_t g = 0; g < G; g++) {
+        int32_t p = f2[level[g]]++;
+        out->order[p] = g;
+        out->pos[g] = p;
+    }
+    // longest path delay (max over arcs of the larger of rise/fall)
+    std::vector<int64_t> pd(G, 0);
+    int64_t best = 0;
+    for (int32_t p = 0; p < G; p++) {
+        int32_t g = out->order[p];
+        int64_t m = 0;
+        for (int32_t a = fanin_off[g]; a < fanin_off[g + 1]; a++) {
+            int64_t in = fanin_net[a] >= n_pi ? pd[fanin_net[a] - n_pi] : 0;
+            m = std::max(m, in + std::max(d_rise[a], d_fall[a]));
+        }
+        pd[g] = m;
+        best = std::max(best, m);
+    }
+    out->max_path_delay = best;
+    out->level = std::move(level);
+    return GLS_OK;
+}
+
+int check_stimulus_host(int32_t n_pi, const int64_t *off, const int32_t *t, const uint8_t *v, bool deep) {
+    if (n_pi < 0 || !off) return fail(GLS_EINVAL, "bad stimulus arguments");
+    if (off[0] != 0) return fail(GLS_ESTIM, "off[0] must be 0");
+    for (int32_t i = 0; i < n_pi; i++)
+        if (off[i + 1] < off[i]) return fail(GLS_ESTIM, "off not monotone at PI %d", i);
+    if (off[n_pi] > 0 && (!t || !v)) return fail(GLS_EINVAL, "NULL stimulus arrays");
+    if (off[n_pi] >= ((int64_t)1 << 32)) return fail(GLS_ESTIM, "more than 2^32 stimulus transitions");
+    if (!deep) return GLS_OK;
+    for (int32_t i = 0; i < n_pi; i++)
+        for (int64_t e = off[i]; e < off[i + 1]; e++) {
+            if (t[e] < 0 || (uint32_t)t[e] >= kTimeLimit) return fail(GLS_ESTIM, "PI %d: time %d out of [0, 2^30-1)", i, t[e]);
+            if (v[e] > 3) return fail(GLS_ESTIM, "PI %d: value %d", i, v[e]);
+            if (e > off[i] && t[e] <= t[e - 1]) return fail(GLS_ESTIM, "PI %d: times not increasing", i);
+            if (e > off[i] && v[e] == v[e - 1]) return fail(GLS_ESTIM, "PI %d: repeated value", i);
+        }
+    return GLS_OK;
+}
+
+// ---- objects --------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct NetlistObj {
+    int32_t n_pi = 0, n_gates = 0;
+    Levelized lv;
+    GateRec *d_gates = nullptr;
+    int32_t *d_ext2int = nullptr;      // [N] caller net id -> internal net id
+    std::vector<int32_t> ext2int;      // host copy
+};
+
+struct StimObj {
+    int32_t n_pi = 0;
+    int64_t n_events = 0, cap_events = 0;
+    uint32_t max_time = 0;
+    int64_t *d_off = nullptr;
+    int32_t *d_t = nullptr;
+    uint8_t *d_v = nullptr;
+    uint32_t *d_packed = nullptr;
+};
+
+struct RunObj {
+    int32_t netlist_id = 0, stim_id = 0;
+    RunDev dev{};
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    unsigned long long *d_sum = nullptr;
+    int64_t *d_off = nullptr;          // [N+1] for read_all
+    int64_t *d_scan_tmp = nullptr;
+    size_t scan_tmp = 0;
+    uint32_t *d_gather = nullptr;
+    int64_t gather_cap = 0;
+    bool launched = false;
+};
+
+}  // namespace
+
+struct gls_ctx {
+    int device = 0;
+    uint64_t budget = 0, used = 0;
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    int sm_count = 0;
+    LevelCfg cfg{8, 0};
+    int32_t next_id = 1;
+    std::unordered_map<int32_t, std::unique_ptr<NetlistObj>> netlists;
+    std::unordered_map<int32_t, std::unique_ptr<StimObj>> stims;
+    std::unordered_map<int32_t, std::unique_ptr<RunObj>> runs;
+    std::unordered_map<void *, size_t> allocs;
+    uint32_t *d_status = nullptr;       // scratch for stimulus packing (3 words)
+};
+
+namespace {
+
+int dalloc(gls_ctx *c, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (c->used + bytes > c->budget)
+        return fail(GLS_ENOMEM, "device budget exceeded (%llu + %llu > %llu bytes)", (unsigned long long)c->used,
+                    (unsigned long long)bytes, (unsigned long long)c->budget);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(GLS_ENOMEM, "cudaMalloc(%llu): %s", (unsigned long long)bytes, cudaGetErrorString(e));
+    }
+    c->used += bytes;
+    c->allocs[*p] = bytes;
+    return GLS_OK;
+}
+
+template <class T>
+int dalloc_n(gls_ctx *c, T **p, size_t n) {
+    void *q = nullptr;
+    int rc = dalloc(c, &q, n * sizeof(T));
+    *p = static_cast<T *>(q);
+    return rc;
+}
+
+void dfree(gls_ctx *c, void *p) {
+    if (!p) return;
+    auto it = c->allocs.find(p);
+    if (it != c->allocs.end()) {
+        c->used -= it->second;
+        c->allocs.erase(it);
+    }
+    cudaFree(p);
+}
+
+void free_netlist(gls_ctx *c, NetlistObj *n) {
+    dfree(c, n->d_gates);
+    dfree(c, n->d_ext2int);
+}
+void free_stim(gls_ctx *c, StimObj *s) {
+    dfree(c, s->d_off);
+    dfree(c, s->d_t);
+    dfree(c, s->d_v);
+    dfree(c, s->d_packed);
+}
+void free_run(gls_ctx *c, RunObj *r) {
+    if (r->exec) cudaGraphExecDestroy(r->exec);
+    if (r->ev0) cudaEventDestroy(r->ev0);
+    if (r->ev1) cudaEventDestroy(r->ev1);
+    dfree(c, r->dev.net_ptr);
+    dfree(c, r->dev.net_len);
+    dfree(c, r->dev.arena);
+    dfree(c, r->dev.arena_top);
+    dfree(c, r->dev.status);
+    dfree(c, r->dev.level_ctr);
+    dfree(c, r->d_sum);
+    dfree(c, r->d_off);
+    dfree(c, r->d_scan_tmp);
+    dfree(c, r->d_gather);
+}
+
+cudaStream_t pick_stream(gls_ctx *c, void *s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
+
+int upload_stimulus(gls_ctx *c, StimObj *s, const int64_t *off, const int32_t *t, const uint8_t *v) {
+    const int64_t E = off[s->n_pi];
+    CK(cudaMemcpyAsync(s->d_off, off, sizeof(int64_t) * (size_t)(s->n_pi + 1), cudaMemcpyHostToDevice, c->stream));
+    if (E > 0) {
+        CK(cudaMemcpyAsync(s->d_t, t, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(s->d_v, v, (size_t)E, cudaMemcpyHostToDevice, c->stream));
+    }
+    const uint32_t init[3] = {0u, 0xFFFFFFFFu, 0u};
+    CK(cudaMemcpyAsync(c->d_status, init, sizeof init, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_pack_stimulus(s->d_off, s->d_t, s->d_v, s->n_pi, s->d_packed, c->d_status, c->stream));
+    uint32_t st[3];
+    CK(cudaMemcpyAsync(st, c->d_status, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (st[0]) {
+        // the device found a violation; name the first rule broken on the host
+        int rc = check_stimulus_host(s->n_pi, off, t, v, true);
+        return rc ? rc : fail(GLS_ESTIM, "stimulus rule violated at PI %u", st[1]);
+    }
+    s->n_events = E;
+    s->max_time = st[2];
+    return GLS_OK;
+}
+
+NetlistObj *find_netlist(gls_ctx *c, int32_t id) {
+    auto it = c->netlists.find(id);
+    return it == c->netlists.end() ? nullptr : it->second.get();
+}
+StimObj *find_stim(gls_ctx *c, int32_t id) {
+    auto it = c->stims.find(id);
+    return it == c->stims.end() ? nullptr : it->second.get();
+}
+RunObj *find_run(gls_ctx *c, int32_t id) {
+    auto it = c->runs.find(id);
+    return it == c->runs.end() ? nullptr : it->second.get();
+}
+
+int build_run_graph(gls_ctx *c, RunObj *r, NetlistObj *n, StimObj *s) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch_run_init(s->d_off, s->d_packed, n->n_pi, r->dev, n->lv.depth, c->cap_stream);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(r->ev0, c->cap_stream, cudaEventRecordExternal);
+    for (int32_t L = 1; L <= n->lv.depth && e == cudaSuccess; L++) {
+        int32_t b = n->lv.level_begin[L], cnt = n->lv.level_begin[L + 1] - b;
+        e = launch_level(n->d_gates, b, cnt, L - 1, r->dev, c->cfg, c->cap_stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(r->ev1, c->cap_stream, cudaEventRecordExternal);
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(GLS_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&r->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(GLS_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    return GLS_OK;
+}
+
+int time_range_check(NetlistObj *n, StimObj *s) {
+    if ((int64_t)s->max_time + n->lv.max_path_delay >= (int64_t)kTimeLimit)
+        return fail(GLS_ERANGE, "latest input time %u + longest path delay %lld reaches 2^30-1", s->max_time,
+                    (long long)n->lv.max_path_delay);
+    return GLS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+int gls_version(void) { return 100; }
+
+int gls_cell_arity(int cell) { return (cell >= 0 && cell < GLS_NCELLS) ? kArity[cell] : GLS_EINVAL; }
+
+int gls_check_netlist(int32_t n_pi, int32_t n_gates, const uint8_t *type, const int32_t *fanin_off,
+                      const int32_t *fanin_net, const int32_t *d_rise, const int32_t *d_fall, int32_t *depth_out,
+                      int32_t *level_out) {
+    try {
+        Levelized lv;
+        int rc = analyse_netlist(n_pi, n_gates, type, fanin_off, fanin_net, d_rise, d_fall, &lv);
+        if (rc) return rc;
+        if (depth_out) *depth_out = lv.depth;
+        if (level_out) std::copy(lv.level.begin(), lv.level.end(), level_out);
+        return GLS_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(GLS_ENOMEM, "host allocation failed");
+    }
+}
+
+int gls_check_stimulus(int32_t n_pi, const int64_t *off, const int32_t *t, const uint8_t *v) {
+    return check_stimulus_host(n_pi, off, t, v, true);
+}
+
+int gls_create(gls_ctx **out, int device, uint64_t hbm_budget_bytes) {
+    if (!out) return fail(GLS_EINVAL, "out is NULL");
+    *out = nullptr;
+    try {
+        int ndev = 0;
+        CK(cudaGetDeviceCount(&ndev));
+        if (device < 0 || device >= ndev) return fail(GLS_EINVAL, "device %d of %d", device, ndev);
+        CK(cudaSetDevice(device));
+        auto c = std::make_unique<gls_ctx>();
+        c->device = device;
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        c->budget = hbm_budget_bytes ? hbm_budget_bytes : (uint64_t)(0.9 * (double)fr);
+        CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+        CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        uint64_t lut[GLS_NCELLS][2];
+        build_luts(lut);
+        set_luts(lut, GLS_NCELLS);
+        CK(cudaGetLastError());
+        int per_sm = level_max_ctas_per_sm(c->cfg.warps_per_cta);
+        CK(cudaGetLastError());
+        if (per_sm < 1) return fail(GLS_ECUDA, "level kernel does not fit on an SM");
+        c->cfg.ctas = per_sm * c->sm_count;
+        int rc = dalloc_n(c.get(), &c->d_status, 4);
+        if (rc) return rc;
+        *out = c.release();
+        return GLS_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(GLS_ENOMEM, "host allocation failed");
+    }
+}
+
+void gls_destroy(gls_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto &kv : c->runs) free_run(c, kv.second.get());
+    for (auto &kv : c->stims) free_stim(c, kv.second.get());
+    for (auto &kv : c->netlists) free_netlist(c, kv.second.get());
+    dfree(c, c->d_status);
+    cudaStreamDestroy(c->stream);
+    cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+const char *gls_last_error(gls_ctx *) { return g_err.c_str(); }
+
+int gls_load_netlist(gls_ctx *c, int32_t n_pi, int32_t n_gates, const uint8_t *type, const int32_t *fanin_off,
+                     const int32_t *fanin_net, const int32_t *d_rise, const int32_t *d_fall, int32_t *netlist_id) {
+    if (!c || !netlist_id) return fail(GLS_EINVAL, "NULL argument");
+    try {
+        CK(cudaSetDevice(c->device));
+        auto n = std::make_unique<NetlistObj>();
+        int rc = analyse_netlist(n_pi, n_gates, type, fanin_off, fanin_net, d_rise, d_fall, &n->lv);
+        if (rc) return rc;
+        n->n_pi = n_pi;
+        n->n_gates = n_gates;
+        const int64_t N = (int64_t)n_pi + n_gates;
+        std::vector<GateRec> recs(std::max<int32_t>(n_gates, 1));
+        for (int32_t p = 0; p < n_gates; p++) {
+            const int32_t g = n->lv.order[p];
+            GateRec &r = recs[p];
+            std::memset(&r, 0, sizeof r);
+            r.type = type[g];
+            r.k = (uint8_t)kArity[type[g]];
+            r.out_net = (uint32_t)(n_pi + p);
+            int32_t dmin = INT32_MAX;
+            for (int q = 0; q < r.k; q++) {
+                const int32_t a = fanin_off[g] + q, net = fanin_net[a];
+                r.fin[q] = net < n_pi ? net : n_pi + n->lv.pos[net - n_pi];
+                r.rise[q] = d_rise[a];
+                r.fall[q] = d_fall[a];
+                dmin = std::min(dmin, std::min(d_rise[a], d_fall[a]));
+            }
+            r.dmin = dmin;
+        }
+        n->ext2int.resize(N);
+        for (int32_t i = 0; i < n_pi; i++) n->ext2int[i] = i;
+        for (int32_t g = 0; g < n_gates; g++) n->ext2int[n_pi + g] = n_pi + n->lv.pos[g];
+        rc = dalloc_n(c, &n->d_gates, recs.size());
+        if (!rc) rc = dalloc_n(c, &n->d_ext2int, (size_t)std::max<int64_t>(N, 1));
+        if (rc) { free_netlist(c, n.get()); return rc; }
+        CK(cudaMemcpyAsync(n->d_gates, recs.data(), sizeof(GateRec) * recs.size(), cudaMemcpyHostToDevice, c->stream));
+        if (N > 0)
+            CK(cudaMemcpyAsync(n->d_ext2int, n->ext2int.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        const int32_t id = c->next_id++;
+        c->netlists[id] = std::move(n);
+        *netlist_id = id;
+        return GLS_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(GLS_ENOMEM, "host allocation failed");
+    }
+}
+
+int gls_load_stimulus(gls_ctx *c, int32_t n_pi, const int64_t *off, const int32_t *t, const uint8_t *v,
+                      int32_t *stim_id) {
+    if (!c || !stim_id) return fail(GLS_EINVAL, "NULL argument");
+    try {
+        CK(cudaSetDevice(c->device));
+        int rc = check_stimulus_host(n_pi, off, t, v, false);
+        if (rc) return rc;
+        auto s = std::make_unique<StimObj>();
+        s->n_pi = n_pi;
+        s->cap_events = off[n_pi];
+        rc = dalloc_n(c, &s->d_off, (size_t)n_pi + 1);
+        if (!rc) rc = dalloc_n(c, &s->d_t, (size_t)std::max<int64_t>(s->cap_events, 1));
+        if (!rc) rc = dalloc_n(c, &s->d_v, (size_t)std::max<int64_t>(s->cap_events, 1));
+        if (!rc) rc = dalloc_n(c, &s->d_packed, (size_t)stim_words(s->cap_events, n_pi));
+        if (!rc) rc = upload_stimulus(c, s.get(), off, t, v);
+        if (rc) { free_stim(c, s.get()); return rc; }
+        const int32_t id = c->next_id++;
+        c->stims[id] = std::move(s);
+        *stim_id = id;
+        return GLS_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(GLS_ENOMEM, "host allocation failed");
+    }
+}
+
+int gls_update_stimulus(gls_ctx *c, int32_t stim_id, const int64_t *off, const int32_t *t, const uint8_t *v) {
+    if (!c) return fail(GLS_EINVAL, "NULL context");
+    StimObj *s = find_stim(c, stim_id);
+    if (!s) return fail(GLS_EINVAL, "unknown stimulus id %d", stim_id);
+    CK(cudaSetDevice(c->device));
+    int rc = check_stimulus_host(s->n_pi, off, t, v, false);
+    if (rc) return rc;
+    if (off[s->n_pi] > s->cap_events)
+        return fail(GLS_EOVERFLOW, "%lld transitions exceed the stimulus capacity %lld", (long long)off[s->n_pi],
+                    (long long)s->cap_events);
+    // runs reading this stimulus may still be in flight on other streams
+    CK(cudaDeviceSynchronize());
+    return upload_stimulus(c, s, off, t, v);
+}
+
+int gls_simulate(gls_ctx *c, int32_t netlist_id, int32_t stim_id, int64_t arena_events, void *cuda_stream,
+                 int32_t *run_id) {
+    if (!c || !run_id) return fail(GLS_EINVAL, "NULL argument");
+    try {
+        CK(cudaSetDevice(c->device));
+        NetlistObj *n = find_netlist(c, netlist_id);
+        StimObj *s = find_stim(c, stim_id);
+        if (!n) return fail(GLS_EINVAL, "unknown netlist id %d", netlist_id);
+        if (!s) return fail(GLS_EINVAL, "unknown stimulus id %d", stim_id);
+        if (s->n_pi != n->n_pi) return fail(GLS_EINVAL, "stimulus has %d PIs, netlist %d", s->n_pi, n->n_pi);
+        int rc = time_range_check(n, s);
+        if (rc) return rc;
+        const int64_t N = (int64_t)n->n_pi + n->n_gates;
+        if (arena_events <= 0) {
+            // default: 256 words per stimulus transition plus 1 Mi, at most half
+            // of what is left of the budget (GLS_EOVERFLOW reports the demand)
+            uint64_t left = c->budget > c->used ? c->budget - c->used : 0;
+            uint64_t meta = (uint64_t)N * 12 + (uint64_t)n->lv.depth * 4 + 4096;
+            uint64_t cap = left > meta ? (left - meta) / 2 / 4 : 0;
+            uint64_t want = 256ull * (uint64_t)s->n_events + (1ull << 20);
+            arena_events = (int64_t)std::min(cap, want);
+        }
+        auto r = std::make_unique<RunObj>();
+        r->netlist_id = netlist_id;
+        r->stim_id = stim_id;
+        r->dev.arena_cap = (uint64_t)arena_events;
+        rc = dalloc_n(c, &r->dev.net_ptr, (size_t)std::max<int64_t>(N, 1));
+        if (!rc) rc = dalloc_n(c, &r->dev.net_len, (size_t)std::max<int64_t>(N, 1));
+        if (!rc) rc = dalloc_n(c, &r->dev.arena, (size_t)std::max<int64_t>(arena_events, 4));
+        if (!rc) rc = dalloc_n(c, &r->dev.arena_top, 1);
+        if (!rc) rc = dalloc_n(c, &r->dev.status, 1);
+        if (!rc) rc = dalloc_n(c, &r->dev.level_ctr, (size_t)std::max(n->lv.depth, 1));
+        if (!rc) rc = dalloc_n(c, &r->d_sum, 1);
+        if (rc) { free_run(c, r.get()); return rc; }
+        cudaError_t e = cudaEventCreate(&r->ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
+        if (e != cudaSuccess) { free_run(c, r.get()); return fail(GLS_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e)); }
+        rc = build_run_graph(c, r.get(), n, s);
+        if (rc) { free_run(c, r.get()); return rc; }
+        e = cudaGraphLaunch(r->exec, pick_stream(c, cuda_stream));
+        if (e != cudaSuccess) { free_run(c, r.get()); return fail(GLS_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e)); }
+        r->launched = true;
+        const int32_t id = c->next_id++;
+        c->runs[id] = std::move(r);
+        *run_id = id;
+        return GLS_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(GLS_ENOMEM, "host allocation failed");
+    }
+}
+
+int gls_rerun(gls_ctx *c, int32_t run_id, void *cuda_stream) {
+    if (!c) return fail(GLS_EINVAL, "NULL context");
+    RunObj *r = find_run(c, run_id);
+    if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    NetlistObj *n = find_netlist(c, r->netlist_id);
+    StimObj *s = find_stim(c, r->stim_id);
+    if (!n || !s) return fail(GLS_EINVAL, "run %d lost its netlist or stimulus", run_id);
+    int rc = time_range_check(n, s);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    CK(cudaGraphLaunch(r->exec, pick_stream(c, cuda_stream)));
+    return GLS_OK;
+}
+
+int gls_run_stats(gls_ctx *c, int32_t run_id, int64_t *total_events, double *kernel_ms) {
+    if (!c) return fail(GLS_EINVAL, "NULL context");
+    RunObj *r = find_run(c, run_id);
+    if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    NetlistObj *n = find_netlist(c, r->netlist_id);
+    CK(cudaSetDevice(c->device));
+    CK(cudaEventSynchronize(r->ev1));
+    uint32_t status = 0;
+    unsigned long long top = 0, sum = 0;
+    CK(cudaMemcpyAsync(&status, r->dev.status, sizeof status, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&top, r->dev.arena_top, sizeof top, cudaMemcpyDeviceToHost, c->stream));
+    const int64_t N = (int64_t)n->n_pi + n->n_gates;
+    CK(launch_sum_gate_lengths(r->dev.net_len, n->n_pi, N, r->d_sum, c->stream));
+    CK(cudaMemcpyAsync(&sum, r->d_sum, sizeof sum, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (kernel_ms) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r->ev0, r->ev1));
+        *kernel_ms = ms;
+    }
+    if (status & kStArenaOverflow) {
+        if (total_events) *total_events = (int64_t)top;
+        return fail(GLS_EOVERFLOW, "event arena of %llu transitions too small; the run needs %llu",
+                    (unsigned long long)r->dev.arena_cap, top);
+    }
+    if (total_events) *total_events = (int64_t)sum;
+    if (status & kStPendingOverflow) return fail(GLS_ERANGE, "a cell's pending transitions exceeded the device buffer");
+    if (status & kStTimeRange) return fail(GLS_ERANGE, "a computed time reached 2^30-1");
+    return GLS_OK;
+}
+
+int gls_read_waveform(gls_ctx *c, int32_t run_id, int32_t net, int32_t *t, uint8_t *v, int64_t cap, int64_t *n_out) {
+    if (!c) return fail(GLS_EINVAL, "NULL context");
+    RunObj *r = find_run(c, run_id);
+    if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    NetlistObj *n = find_netlist(c, r->netlist_id);
+    const int64_t N = (int64_t)n->n_pi + n->n_gates;
+    if (net < 0 || net >= N) return fail(GLS_EINVAL, "net %d out of range", net);
+    CK(cudaSetDevice(c->device));
+    CK(cudaEventSynchronize(r->ev1));
+    const int32_t in = n->ext2int[net];
+    uint64_t ptr = 0;
+    uint32_t len = 0;
+    CK(cudaMemcpy(&ptr, r->dev.net_ptr + in, sizeof ptr, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&len, r->dev.net_len + in, sizeof len, cudaMemcpyDeviceToHost));
+    if (n_out) *n_out = len;
+    if ((int64_t)len > cap) return fail(GLS_EOVERFLOW, "net %d has %u transitions, cap %lld", net, len, (long long)cap);
+    if (len == 0) return GLS_OK;
+    if (!t || !v) return fail(GLS_EINVAL, "NULL output arrays");
+    try {
+        std::vector<uint32_t> buf(len);
+        CK(cudaMemcpy(buf.data(), reinterpret_cast<const void *>(ptr), sizeof(uint32_t) * len, cudaMemcpyDeviceToHost));
+        for (uint32_t i = 0; i < len; i++) {
+            t[i] = (int32_t)(buf[i] >> 2);
+            v[i] = (uint8_t)(buf[i] & 3u);
+        }
+    } catch (const std::bad_alloc &) {
+        return fail(GLS_ENOMEM, "host allocation failed");
+    }
+    return GLS_OK;
+}
+
+int gls_read_all(gls_ctx *c, int32_t run_id, int64_t *off, uint32_t *packed, int64_t cap) {
+    if (!c || !off) return fail(GLS_EINVAL, "NULL argument");
+    RunObj *r = find_run(c, run_id);
+    if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    NetlistObj *n = find_netlist(c, r->netlist_id);
+    const int64_t N = (int64_t)n->n_pi + n->n_gates;
+    CK(cudaSetDevice(c->device));
+    CK(cudaEventSynchronize(r->ev1));
+    int rc = GLS_OK;
+    if (!r->d_off) {
+        r->scan_tmp = scan_tmp_elems(N + 1);
+        rc = dalloc_n(c, &r->d_off, (size_t)N + 1);
+        if (!rc) rc = dalloc_n(c, &r->d_scan_tmp, r->scan_tmp);
+        if (rc) return rc;
+    }
+    CK(launch_gather_lengths(r->dev.net_len, n->d_ext2int, N, r->d_off, c->stream));
+    CK(launch_exclusive_scan_i64(r->d_off, N + 1, r->d_scan_tmp, r->scan_tmp, c->stream));
+    CK(cudaMemcpyAsync(off, r->d_off, sizeof(int64_t) * (size_t)(N + 1), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int64_t total = off[N];
+    if (total > cap) return fail(GLS_EOVERFLOW, "%lld transitions, cap %lld", (long long)total, (long long)cap);
+    if (total == 0) return GLS_OK;
+    if (!packed) return fail(GLS_EINVAL, "NULL packed array");
+    if (total > r->gather_cap) {
+        dfree(c, r->d_gather);
+        r->d_gather = nullptr;
+        r->gather_cap = 0;
+        rc = dalloc_n(c, &r->d_gather, (size_t)total);
+        if (rc) return rc;
+        r->gather_cap = total;
+    }
+    CK(launch_gather_events(r->dev.net_ptr, r->dev.net_len, n->d_ext2int, r->d_off, N, r->d_gather, c->stream));
+    CK(cudaMemcpyAsync(packed, r->d_gather, sizeof(uint32_t) * (size_t)total, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return GLS_OK;
+}
+
+int gls_release(gls_ctx *c, int32_t id) {
+    if (!c) return fail(GLS_EINVAL, "NULL context");
+    cudaSetDevice(c->device);
+    if (auto it = c->runs.find(id); it != c->runs.end()) {
+        cudaEventSynchronize(it->second->ev1);
+        free_run(c, it->second.get());
+        c->runs.erase(it);
+        return GLS_OK;
+    }
+    for (auto &kv : c->runs)
+        if (kv.second->netlist_id == id || kv.second->stim_id == id)
+            return fail(GLS_EINVAL, "id %d is still used by run %d", id, kv.first);
+    if (auto it = c->stims.find(id); it != c->stims.end()) {
+        free_stim(c, it->second.get());
+        c->stims.erase(it);
+        return GLS_OK;
+    }
+    if (auto it = c->netlists.find(id); it != c->netlists.end()) {
+        free_netlist(c, it->second.get());
+        c->netlists.erase(it);
+        return GLS_OK;
+    }
+    return fail(GLS_EINVAL, "unknown id %d", id);
+}
+
+}  // extern "C"

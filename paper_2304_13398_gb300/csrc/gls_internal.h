@@ -1,0 +1,81 @@
+// gls_internal.h -- device data layout and launch wrappers shared by the
+// translation units of libgls.so.  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gls {
+
+// One transition on the device: (time << 2) | value.  Every time must stay
+// below kTimeLimit = 2^30 - 1 so that it fits 30 bits and stays below the
+// time field of the all-ones sentinel word.  Values: 0, 1, 2 = X, 3 = Z.
+constexpr uint32_t kVX = 2;
+constexpr uint32_t kTimeLimit = (1u << 30) - 1u;   // exclusive
+constexpr uint32_t kTimeInf = 0xFFFFFFFFu;     // "no more transitions"
+
+// Device gate record, gates stored in level order (48 bytes, 16-byte aligned).
+// fin[] are internal net ids: 0..n_pi-1 primary inputs, n_pi+i internal gate i.
+struct __align__(16) GateRec {
+    int32_t fin[3];
+    int32_t rise[3];
+    int32_t fall[3];
+    int32_t dmin;        // min over the arcs of min(rise, fall)
+    uint32_t out_net;    // internal net id of the output (n_pi + i)
+    uint8_t type, k, pad0, pad1;
+};
+static_assert(sizeof(GateRec) == 48, "GateRec layout");
+
+// Status bits a run's kernels may raise.
+enum : uint32_t {
+    kStArenaOverflow = 1u,    // output arena too small
+    kStPendingOverflow = 2u,  // a cell's pending transitions exceeded the buffer
+    kStTimeRange = 4u,        // a computed time reached 2^30
+};
+
+// Per-run device state.
+struct RunDev {
+    uint64_t *net_ptr;        // [N] device address of net n's first transition
+    uint32_t *net_len;        // [N] transition count of net n
+    uint32_t *arena;          // [arena_cap] gate output transitions
+    uint64_t arena_cap;       // capacity in transitions
+    unsigned long long *arena_top;  // bump pointer (transitions), counts demand past cap
+    uint32_t *status;         // kSt* bits
+    int32_t *level_ctr;       // [depth] work counters, zeroed per run
+};
+
+// Level kernel configuration (chosen per launch).
+struct LevelCfg {
+    int warps_per_cta;
+    int ctas;
+};
+
+// Stimulus device layout: PI i's packed transitions start at word
+// stim_base(off[i], i) = (off[i] + 3 i + 3) & ~3 (16-byte aligned, disjoint).
+__host__ __device__ inline uint64_t stim_slot(int64_t off_i, int64_t i) {
+    return (uint64_t)((off_i + 3 * i + 3) & ~(int64_t)3);
+}
+__host__ __device__ inline uint64_t stim_words(int64_t n_events, int64_t n_pi) {
+    return (uint64_t)(n_events + 3 * n_pi + 4);
+}
+
+// ---- launch wrappers (gls_kernels.cu) ----
+void set_luts(const uint64_t lut[][2], int ncells);
+cudaError_t launch_pack_stimulus(const int64_t *d_off, const int32_t *d_t, const uint8_t *d_v, int32_t n_pi,
+                                 uint32_t *d_packed, uint32_t *d_status, cudaStream_t s);
+cudaError_t launch_run_init(const int64_t *d_stim_off, const uint32_t *d_stim_packed, int32_t n_pi,
+                            const RunDev &r, int32_t depth, cudaStream_t s);
+cudaError_t launch_level(const GateRec *d_gates, int32_t g_begin, int32_t g_count, int32_t level,
+                         const RunDev &r, const LevelCfg &cfg, cudaStream_t s);
+size_t level_smem_bytes(int warps_per_cta);
+int level_max_ctas_per_sm(int warps_per_cta);
+cudaError_t launch_gather_lengths(const uint32_t *d_net_len, const int32_t *d_ext2int, int64_t n,
+                                  int64_t *d_off, cudaStream_t s);
+cudaError_t launch_exclusive_scan_i64(int64_t *d_data, int64_t n, int64_t *d_tmp, size_t tmp_elems,
+                                      cudaStream_t s);
+size_t scan_tmp_elems(int64_t n);
+cudaError_t launch_gather_events(const uint64_t *d_net_ptr, const uint32_t *d_net_len, const int32_t *d_ext2int,
+                                 const int64_t *d_off, int64_t n, uint32_t *d_out, cudaStream_t s);
+cudaError_t launch_sum_gate_lengths(const uint32_t *d_net_len, int32_t n_pi, int64_t n, unsigned long long *d_sum,
+                                    cudaStream_t s);
+
+}  // namespace gls

@@ -1,0 +1,245 @@
+"""ctypes binding of libgls.so (declared in include/gls.h).
+
+The module-level ``gls_*`` names are the C entry points themselves with their
+argument types declared; ``Context`` wraps them with numpy marshalling and
+raises ``GlsError`` on a negative status.  All computation happens in the
+library's CUDA kernels: there is no Python or CPU fallback, and loading fails
+loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgls.so")
+
+GLS_OK, GLS_EINVAL, GLS_ECYCLE, GLS_ESTIM, GLS_ERANGE, GLS_ENOMEM, GLS_EOVERFLOW, GLS_ETIMEOUT, GLS_ECUDA = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+STATUS_NAMES = {0: "GLS_OK", -1: "GLS_EINVAL", -2: "GLS_ECYCLE", -3: "GLS_ESTIM", -4: "GLS_ERANGE",
+                -5: "GLS_ENOMEM", -6: "GLS_EOVERFLOW", -7: "GLS_ETIMEOUT", -8: "GLS_ECUDA"}
+CELLS = ["INV", "BUF", "AND2", "OR2", "NAND2", "NOR2", "XOR2", "XNOR2", "MUX2", "AOI21", "OAI21"]
+GLS_MAX_DELAY_SPREAD = 255
+
+P = ctypes.c_void_p
+i32, i64, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+
+# (name, restype, argtypes) of every entry point in include/gls.h
+SIGNATURES = [
+    ("gls_version", ctypes.c_int, []),
+    ("gls_cell_arity", ctypes.c_int, [ctypes.c_int]),
+    ("gls_check_netlist", ctypes.c_int, [i32, i32, P, P, P, P, P, P, P]),
+    ("gls_check_stimulus", ctypes.c_int, [i32, P, P, P]),
+    ("gls_create", ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, u64]),
+    ("gls_destroy", None, [P]),
+    ("gls_last_error", ctypes.c_char_p, [P]),
+    ("gls_load_netlist", ctypes.c_int, [P, i32, i32, P, P, P, P, P, ctypes.POINTER(i32)]),
+    ("gls_load_stimulus", ctypes.c_int, [P, i32, P, P, P, ctypes.POINTER(i32)]),
+    ("gls_update_stimulus", ctypes.c_int, [P, i32, P, P, P]),
+    ("gls_simulate", ctypes.c_int, [P, i32, i32, i64, P, ctypes.POINTER(i32)]),
+    ("gls_rerun", ctypes.c_int, [P, i32, P]),
+    ("gls_run_stats", ctypes.c_int, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]),
+    ("gls_read_waveform", ctypes.c_int, [P, i32, i32, P, P, i64, ctypes.POINTER(i64)]),
+    ("gls_read_all", ctypes.c_int, [P, i32, P, P, i64]),
+    ("gls_release", ctypes.c_int, [P, i32]),
+]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libgls.so and declare every signature.  Raises if it is missing:
+    the simulator has no fallback path."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_2304_13398_gb300.build.build() "
+                               "(the simulator has no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+            globals()[name] = f
+        _lib = lib
+    return _lib
+
+
+def __getattr__(name):
+    if name.startswith("gls_"):
+        load_library()
+        if name in globals():
+            return globals()[name]
+    raise AttributeError(name)
+
+
+class GlsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(P)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)    # torch.cuda.Stream
+
+
+def check_netlist(n_pi, type, fanin_off, fanin_net, d_rise, d_fall):
+    """Host-only validation and levelization; returns (depth, level[G])."""
+    lib = load_library()
+    typ, fo, fn = _c(type, np.uint8), _c(fanin_off, np.int32), _c(fanin_net, np.int32)
+    dr, df = _c(d_rise, np.int32), _c(d_fall, np.int32)
+    depth = ctypes.c_int32(0)
+    level = np.zeros(len(typ), np.int32)
+    rc = lib.gls_check_netlist(n_pi, len(typ), _p(typ), _p(fo), _p(fn), _p(dr), _p(df),
+                               ctypes.cast(ctypes.pointer(depth), P), _p(level))
+    if rc:
+        raise GlsError(rc, lib.gls_last_error(None).decode())
+    return depth.value, level
+
+
+def check_stimulus(n_pi, off, t, v):
+    lib = load_library()
+    rc = lib.gls_check_stimulus(n_pi, _p(_c(off, np.int64)), _p(_c(t, np.int32)), _p(_c(v, np.uint8)))
+    if rc:
+        raise GlsError(rc, lib.gls_last_error(None).decode())
+
+
+@dataclass
+class RunStats:
+    total_events: int
+    kernel_ms: float
+
+
+class Context:
+    """One simulator context on one CUDA device (owns all its device memory)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.lib = load_library()
+        h = P()
+        rc = self.lib.gls_create(ctypes.byref(h), device, hbm_budget_bytes)
+        if rc:
+            raise GlsError(rc, self.lib.gls_last_error(None).decode())
+        self.h = h
+        self.n_nets = {}
+
+    def _ck(self, rc):
+        if rc:
+            raise GlsError(rc, self.lib.gls_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gls_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def load_netlist(self, nl) -> int:
+        typ, fo, fn = _c(nl.type, np.uint8), _c(nl.fanin_off, np.int32), _c(nl.fanin_net, np.int32)
+        dr, df = _c(nl.d_rise, np.int32), _c(nl.d_fall, np.int32)
+        nid = ctypes.c_int32(0)
+        self._ck(self.lib.gls_load_netlist(self.h, int(nl.n_pi), len(typ), _p(typ), _p(fo), _p(fn),
+                                           _p(dr), _p(df), ctypes.byref(nid)))
+        self.n_nets[nid.value] = int(nl.n_pi) + len(typ)
+        return nid.value
+
+    def load_stimulus(self, st, n_pi: int | None = None) -> int:
+        off, t, v = _c(st.off, np.int64), _c(st.t, np.int32), _c(st.v, np.uint8)
+        sid = ctypes.c_int32(0)
+        n_pi = len(off) - 1 if n_pi is None else n_pi
+        self._ck(self.lib.gls_load_stimulus(self.h, n_pi, _p(off), _p(t), _p(v), ctypes.byref(sid)))
+        return sid.value
+
+    def update_stimulus(self, stim_id: int, off, t, v):
+        """off/t/v may be numpy arrays or (pinned) torch CPU tensors."""
+        self._ck(self.lib.gls_update_stimulus(self.h, stim_id, _ptr(off, np.int64), _ptr(t, np.int32),
+                                              _ptr(v, np.uint8)))
+
+    def simulate(self, netlist_id: int, stim_id: int, arena_events: int = 0, stream=None) -> int:
+        rid = ctypes.c_int32(0)
+        self._ck(self.lib.gls_simulate(self.h, netlist_id, stim_id, arena_events, _stream_handle(stream),
+                                       ctypes.byref(rid)))
+        self.n_nets[rid.value] = self.n_nets[netlist_id]
+        return rid.value
+
+    def rerun(self, run_id: int, stream=None):
+        self._ck(self.lib.gls_rerun(self.h, run_id, _stream_handle(stream)))
+
+    def run_stats(self, run_id: int) -> RunStats:
+        tot, ms = ctypes.c_int64(0), ctypes.c_double(0.0)
+        self._ck(self.lib.gls_run_stats(self.h, run_id, ctypes.byref(tot), ctypes.byref(ms)))
+        return RunStats(tot.value, ms.value)
+
+    def run_stats_raw(self, run_id: int):
+        """(status, total_events, kernel_ms) without raising."""
+        tot, ms = ctypes.c_int64(0), ctypes.c_double(0.0)
+        rc = self.lib.gls_run_stats(self.h, run_id, ctypes.byref(tot), ctypes.byref(ms))
+        return rc, tot.value, ms.value
+
+    def read_waveform(self, run_id: int, net: int):
+        n = ctypes.c_int64(0)
+        rc = self.lib.gls_read_waveform(self.h, run_id, net, None, None, 0, ctypes.byref(n))
+        if rc not in (GLS_OK, GLS_EOVERFLOW):
+            self._ck(rc)
+        t = np.zeros(n.value, np.int32)
+        v = np.zeros(n.value, np.uint8)
+        self._ck(self.lib.gls_read_waveform(self.h, run_id, net, _p(t), _p(v), n.value, ctypes.byref(n)))
+        return t, v
+
+    def read_all(self, run_id: int, off=None, packed=None):
+        """Dense CSR of every net: (off int64[N+1], packed uint32[E]) with
+        packed = (t << 2) | v.  Optional preallocated (pinned) outputs."""
+        N = self.n_nets[run_id]
+        if off is None:
+            off = np.zeros(N + 1, np.int64)
+        if packed is None:
+            rc = self.lib.gls_read_all(self.h, run_id, _ptr(off, np.int64), None, 0)
+            if rc not in (GLS_OK, GLS_EOVERFLOW):
+                self._ck(rc)
+            total = int(off[N])
+            packed = np.zeros(total, np.uint32)
+        cap = int(packed.shape[0]) if hasattr(packed, "shape") else len(packed)
+        self._ck(self.lib.gls_read_all(self.h, run_id, _ptr(off, np.int64), _ptr(packed, np.uint32), cap))
+        return off, packed
+
+    def release(self, obj_id: int):
+        self._ck(self.lib.gls_release(self.h, obj_id))
+
+
+def _ptr(a, dt):
+    """Pointer of a numpy array or a contiguous CPU torch tensor of dtype dt."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"need a contiguous {np.dtype(dt)} array")
+        return _p(a)
+    if hasattr(a, "data_ptr"):
+        return P(a.data_ptr())
+    raise TypeError(type(a))
+
+
+def unpack(packed: np.ndarray):
+    """Split packed transitions into (times int32, values uint8)."""
+    p = np.asarray(packed, dtype=np.uint32)
+    return (p >> 2).astype(np.int32), (p & 3).astype(np.uint8)
