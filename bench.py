@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--gates", type=int, default=0, help="override the recipe's gate count (profiling cases)")
     ap.add_argument("--pis", type=int, default=0, help="override the recipe's primary-input count")
     ap.add_argument("--arena-words", type=int, default=0, help="event arena size (0: size from a first run)")
+    ap.add_argument("--schedule", default="dependency", choices=["dependency", "levels"])
+    ap.add_argument("--warps-per-cta", type=int, default=0)
     return ap.parse_args()
 
 
@@ -255,6 +257,9 @@ def run_own(a):
     w = synth.make_workload(a.workload, seed=a.seed, **overrides(a))
     nl, st = w.netlist, w.stimulus
     ctx = gls.Context(local)
+    ctx.set_schedule(a.schedule)
+    if a.warps_per_cta:
+        ctx.set_option(gls.gls.GLS_OPT_WARPS_PER_CTA, a.warps_per_cta)
     stream = torch.cuda.Stream()
     nid = ctx.load_netlist(nl)
     sid = ctx.load_stimulus(st)
@@ -347,8 +352,8 @@ def run_own(a):
     cfg = describe(a.workload, w)
     cfg.update({"output_transitions_per_step": e_out, "arena_words": int(arena) if arena else "default",
                 "l2_policy": "inputs larger than L2 (stimulus and intermediate waveforms >> 129 MB)",
-                "parallelism": f"replicas{world}" if world > 1 else "single"})
-    launches_per_step = 1 + int(w.recipe["net"]["depth"])
+                "parallelism": f"replicas{world}" if world > 1 else "single", "schedule": a.schedule})
+    launches_per_step = 1 + (1 if a.schedule == "dependency" else int(w.recipe["net"]["depth"]))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": max(a.warmup, 3), "ms_per_step": ms, "sim_time_ms": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32 packed events (int32 time, 2-bit value)",

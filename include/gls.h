@@ -168,12 +168,13 @@ int gls_rerun(gls_ctx *ctx, int32_t run_id, void *cuda_stream);
 /*
  * Wait for a run and report it: *total_events = output transitions of all
  * gates, *kernel_ms = device time of the last enqueued evaluation (CUDA
- * events around the level sequence).  Either pointer may be NULL.
+ * events around the gate kernels).  Either pointer may be NULL.
  * GLS_EOVERFLOW when the event arena was too small: then *total_events is the
  * arena demand of the gates that were evaluated, a lower bound of the full
  * demand because gates that did not fit leave their readers fewer inputs
  * (retry with at least that much), GLS_ERANGE when a cell's pending transitions
- * exceeded the device buffer.
+ * exceeded the device buffer, GLS_ETIMEOUT when a device wait for a fanin
+ * gate gave up (dependency schedule).
  */
 int gls_run_stats(gls_ctx *ctx, int32_t run_id, int64_t *total_events, double *kernel_ms);
 
@@ -193,6 +194,28 @@ int gls_read_waveform(gls_ctx *ctx, int32_t run_id, int32_t net, int32_t *t, uin
  * cap is smaller than the total (off is still filled).  Synchronous.
  */
 int gls_read_all(gls_ctx *ctx, int32_t run_id, int64_t *off, uint32_t *packed, int64_t cap);
+
+/* Context options (gls_set_option); they apply to runs created afterwards. */
+typedef enum gls_option {
+    GLS_OPT_SCHEDULE = 1,       /* GLS_SCHEDULE_LEVELS or GLS_SCHEDULE_DEPENDENCY (default)  */
+    GLS_OPT_WARPS_PER_CTA = 2,  /* warps per CTA of the gate kernels, 1..32 (default 4)        */
+    GLS_OPT_WAIT_LIMIT_MS = 3,  /* bound on one device wait for a fanin gate (default 10000)    */
+    GLS_OPT_TEST_WITHHOLD_GATE = 4  /* test hook for the bounded wait: the gate at this level-order
+                                       position never signals completion, so its readers wait out
+                                       the limit and the run reports GLS_ETIMEOUT (-1 = off)     */
+} gls_option;
+
+/* Schedules of the gate evaluation (Sec. 4.1).
+   LEVELS: one kernel launch per DAG level (the topological-layer partition
+   the paper criticises, kept as the reference form), all in one CUDA graph.
+   DEPENDENCY: one persistent launch; each warp takes the next gate in level
+   order and starts it as soon as its fanin gates are done (Algorithm 1's
+   readiness test, without layer barriers); a wait longer than
+   GLS_OPT_WAIT_LIMIT_MS ends the run with GLS_ETIMEOUT. */
+enum { GLS_SCHEDULE_LEVELS = 0, GLS_SCHEDULE_DEPENDENCY = 1 };
+
+/* Set a context option; GLS_EINVAL for an unknown option or value. */
+int gls_set_option(gls_ctx *ctx, int option, int64_t value);
 
 /* Free a netlist, stimulus or run handle (ids are unique per context). */
 int gls_release(gls_ctx *ctx, int32_t id);

@@ -237,6 +237,7 @@ struct RunObj {
     uint32_t *d_gather = nullptr;
     int64_t gather_cap = 0;
     bool launched = false;
+    int schedule = 0;
 };
 
 }  // namespace
@@ -247,6 +248,9 @@ struct gls_ctx {
     cudaStream_t stream = nullptr, cap_stream = nullptr;
     int sm_count = 0;
     LevelCfg cfg{8, 0};
+    int schedule = GLS_SCHEDULE_DEPENDENCY;
+    uint64_t wait_limit_ns = 10ull * 1000 * 1000 * 1000;
+    int32_t withhold_gate = -1;
     int32_t next_id = 1;
     std::unordered_map<int32_t, std::unique_ptr<NetlistObj>> netlists;
     std::unordered_map<int32_t, std::unique_ptr<StimObj>> stims;
@@ -312,6 +316,7 @@ void free_run(gls_ctx *c, RunObj *r) {
     dfree(c, r->dev.arena_top);
     dfree(c, r->dev.status);
     dfree(c, r->dev.level_ctr);
+    dfree(c, r->dev.done);
     dfree(c, r->d_sum);
     dfree(c, r->d_off);
     dfree(c, r->d_scan_tmp);
@@ -359,11 +364,15 @@ RunObj *find_run(gls_ctx *c, int32_t id) {
 int build_run_graph(gls_ctx *c, RunObj *r, NetlistObj *n, StimObj *s) {
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = launch_run_init(s->d_off, s->d_packed, n->n_pi, r->dev, n->lv.depth, c->cap_stream);
+    cudaError_t e = launch_run_init(s->d_off, s->d_packed, r->dev, n->lv.depth + 1, c->cap_stream);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(r->ev0, c->cap_stream, cudaEventRecordExternal);
-    for (int32_t L = 1; L <= n->lv.depth && e == cudaSuccess; L++) {
-        int32_t b = n->lv.level_begin[L], cnt = n->lv.level_begin[L + 1] - b;
-        e = launch_level(n->d_gates, b, cnt, L - 1, r->dev, c->cfg, c->cap_stream);
+    if (r->schedule == GLS_SCHEDULE_DEPENDENCY) {
+        if (e == cudaSuccess) e = launch_dependency(n->d_gates, n->n_gates, n->lv.depth, r->dev, c->cfg, c->cap_stream);
+    } else {
+        for (int32_t L = 1; L <= n->lv.depth && e == cudaSuccess; L++) {
+            int32_t b = n->lv.level_begin[L], cnt = n->lv.level_begin[L + 1] - b;
+            e = launch_level(n->d_gates, b, cnt, L - 1, r->dev, c->cfg, c->cap_stream);
+        }
     }
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(r->ev1, c->cap_stream, cudaEventRecordExternal);
     cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
@@ -374,6 +383,15 @@ int build_run_graph(gls_ctx *c, RunObj *r, NetlistObj *n, StimObj *s) {
     e = cudaGraphInstantiate(&r->exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(GLS_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    return GLS_OK;
+}
+
+int apply_launch_cfg(gls_ctx *c, int warps_per_cta) {
+    const int per_sm = gate_max_ctas_per_sm(warps_per_cta);
+    CK(cudaGetLastError());
+    if (per_sm < 1) return fail(GLS_EINVAL, "%d warps per CTA do not fit on an SM", warps_per_cta);
+    c->cfg.warps_per_cta = warps_per_cta;
+    c->cfg.ctas = per_sm * c->sm_count;
     return GLS_OK;
 }
 
@@ -432,11 +450,9 @@ int gls_create(gls_ctx **out, int device, uint64_t hbm_budget_bytes) {
         build_luts(lut);
         set_luts(lut, GLS_NCELLS);
         CK(cudaGetLastError());
-        int per_sm = level_max_ctas_per_sm(c->cfg.warps_per_cta);
-        CK(cudaGetLastError());
-        if (per_sm < 1) return fail(GLS_ECUDA, "level kernel does not fit on an SM");
-        c->cfg.ctas = per_sm * c->sm_count;
-        int rc = dalloc_n(c.get(), &c->d_status, 4);
+        int rc = apply_launch_cfg(c.get(), 4);
+        if (rc) return rc;
+        rc = dalloc_n(c.get(), &c->d_status, 4);
         if (rc) return rc;
         *out = c.release();
         return GLS_OK;
@@ -574,12 +590,18 @@ int gls_simulate(gls_ctx *c, int32_t netlist_id, int32_t stim_id, int64_t arena_
         r->netlist_id = netlist_id;
         r->stim_id = stim_id;
         r->dev.arena_cap = (uint64_t)arena_events;
+        r->dev.n_pi = n->n_pi;
+        r->dev.n_gates = n->n_gates;
+        r->dev.wait_limit_ns = c->wait_limit_ns;
+        r->dev.withhold_gate = c->withhold_gate;
+        r->schedule = c->schedule;
         rc = dalloc_n(c, &r->dev.net_ptr, (size_t)std::max<int64_t>(N, 1));
         if (!rc) rc = dalloc_n(c, &r->dev.net_len, (size_t)std::max<int64_t>(N, 1));
         if (!rc) rc = dalloc_n(c, &r->dev.arena, (size_t)std::max<int64_t>(arena_events, 4));
         if (!rc) rc = dalloc_n(c, &r->dev.arena_top, 1);
         if (!rc) rc = dalloc_n(c, &r->dev.status, 1);
-        if (!rc) rc = dalloc_n(c, &r->dev.level_ctr, (size_t)std::max(n->lv.depth, 1));
+        if (!rc) rc = dalloc_n(c, &r->dev.level_ctr, (size_t)n->lv.depth + 1);
+        if (!rc) rc = dalloc_n(c, &r->dev.done, (size_t)std::max(n->n_gates, 1));
         if (!rc) rc = dalloc_n(c, &r->d_sum, 1);
         if (rc) { free_run(c, r.get()); return rc; }
         cudaError_t e = cudaEventCreate(&r->ev0);
@@ -641,6 +663,8 @@ int gls_run_stats(gls_ctx *c, int32_t run_id, int64_t *total_events, double *ker
     if (total_events) *total_events = (int64_t)sum;
     if (status & kStPendingOverflow) return fail(GLS_ERANGE, "a cell's pending transitions exceeded the device buffer");
     if (status & kStTimeRange) return fail(GLS_ERANGE, "a computed time reached 2^30-1");
+    if (status & kStTimeout) return fail(GLS_ETIMEOUT, "a wait for a fanin gate exceeded %.3f s",
+                                         (double)r->dev.wait_limit_ns * 1e-9);
     return GLS_OK;
 }
 
@@ -710,6 +734,30 @@ int gls_read_all(gls_ctx *c, int32_t run_id, int64_t *off, uint32_t *packed, int
     CK(cudaMemcpyAsync(packed, r->d_gather, sizeof(uint32_t) * (size_t)total, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return GLS_OK;
+}
+
+int gls_set_option(gls_ctx *c, int option, int64_t value) {
+    if (!c) return fail(GLS_EINVAL, "NULL context");
+    CK(cudaSetDevice(c->device));
+    switch (option) {
+    case GLS_OPT_SCHEDULE:
+        if (value != GLS_SCHEDULE_LEVELS && value != GLS_SCHEDULE_DEPENDENCY)
+            return fail(GLS_EINVAL, "unknown schedule %lld", (long long)value);
+        c->schedule = (int)value;
+        return GLS_OK;
+    case GLS_OPT_WARPS_PER_CTA:
+        if (value < 1 || value > 32) return fail(GLS_EINVAL, "warps per CTA must be in [1, 32]");
+        return apply_launch_cfg(c, (int)value);
+    case GLS_OPT_WAIT_LIMIT_MS:
+        if (value < 1) return fail(GLS_EINVAL, "wait limit must be >= 1 ms");
+        c->wait_limit_ns = (uint64_t)value * 1000000ull;
+        return GLS_OK;
+    case GLS_OPT_TEST_WITHHOLD_GATE:
+        if (value < -1 || value > INT32_MAX) return fail(GLS_EINVAL, "gate index out of range");
+        c->withhold_gate = (int32_t)value;
+        return GLS_OK;
+    }
+    return fail(GLS_EINVAL, "unknown option %d", option);
 }
 
 int gls_release(gls_ctx *c, int32_t id) {

@@ -1,34 +1,43 @@
-// gls_eval.cu -- the level kernel: one warp evaluates one gate at a time.
+// gls_eval.cu -- gate evaluation kernels: one warp evaluates one gate at a time.
 //
-// For a gate with k <= 3 fanin waveforms the warp streams the fanins in
-// chunks through shared memory and, per chunk:
-//   1. loads a window of up to CH transitions of every pin and cuts the chunk
-//      at T_end, the earliest window end among pins with more transitions
-//      left, so every transition at t <= T_end is present (a timestamp never
-//      straddles two chunks);
-//   2. merges the pins by time with merge-path partitions (pins a and b are
-//      merged first for 3-input cells), each lane taking an equal share;
-//   3. walks its share in time order, applying all transitions of one
-//      timestamp together and, when the cell value changes, producing the
-//      scheduled transition (t + min delay over the pins with a transition at
-//      t, new value) -- Algorithm 2 (Sec. 4.2), minimum delay of Sec. 2.3;
-//   4. applies Eq. 1: a transition survives iff its t_r is below the t_r of
-//      every later one.  Each lane keeps a monotone stack of its own share,
-//      a warp suffix-minimum across lanes finishes the test, and transitions
-//      carried over from the previous chunk are filtered by the chunk minimum;
-//   5. commits every survivor whose t_r is below T_end + 1 + dmin (no later
-//      transition of this gate can reach back that far), dropping one equal
-//      to the value before it (Fig. 6), and carries the rest to the next
-//      chunk (at most dmax - dmin of them).
-// Step 4's scan form equals the paper's sequential "deny and replace": a
-// transition is denied iff a later-determined one has t_r <= its t_r.
+// For a gate with K <= 3 fanin waveforms the warp streams the fanins in
+// chunks through shared memory.  Per chunk:
+//   1. a window of up to CH transitions of every pin sits in shared memory
+//      (copied asynchronously with 16-byte cp.async while the previous chunk
+//      was being evaluated); the chunk is cut at T_end, the earliest window
+//      end among pins with more transitions left, so every transition at
+//      t <= T_end is present and a timestamp never straddles two chunks;
+//   2. the pins are merged by time with merge-path partitions (pins a and b
+//      first for 3-input cells), each lane taking an equal share; an
+//      all-ones sentinel after every window removes bounds checks;
+//   3. each lane walks its share in time order, applying all transitions of
+//      one timestamp together, and when the cell value changes produces the
+//      scheduled transition (t + min delay over the pins with a transition
+//      at t, new value) -- Algorithm 2, minimum delay of Sec. 2.3;
+//   4. Eq. 1: a transition survives iff its t_r is below the t_r of every
+//      later one.  Each lane keeps a monotone stack of its own share, a warp
+//      suffix minimum across lanes finishes the test, and transitions carried
+//      over from the previous chunk are filtered by the chunk minimum;
+//   5. every survivor with t_r < T_end + 1 + dmin is final (no later
+//      transition of this gate can reach back that far): it is written out
+//      unless it equals the value before it (Fig. 6); the rest is carried to
+//      the next chunk (at most dmax - dmin transitions).
+// Step 4's scan form equals the sequential "deny and replace" of Sec. 2.3:
+// a transition is denied iff a later-determined one has t_r <= its t_r.
 //
 // Output allocation: before evaluating, the warp reserves the Eq. 2 bound
-// (sum of fanin lengths, >= the number of distinct input timestamps >= the
-// output length) from the run's event arena with one atomicAdd, writes the
-// waveform into it and records (address, length) in the net descriptors.  Net
-// descriptors are read by the next levels only, so all waveform loads may go
-// through the read-only path.
+// (sum of fanin lengths >= distinct input timestamps >= output length),
+// rounded up to 4 words, from the run's event arena with one atomicAdd and
+// records (address, length) in the net descriptors when done.
+//
+// Two schedules share the gate code:
+//   level mode       one launch per level (captured in one CUDA graph); the
+//                    launch boundary orders a level after the one before;
+//   dependency mode  one persistent launch for all gates (Algorithm 1): a
+//                    warp takes the next gate in level order and waits, with
+//                    a bounded spin, until each fanin gate has published its
+//                    waveform (release/acquire flags), so no level barrier
+//                    holds work back behind the longest gate of a level.
 #include "gls_internal.h"
 
 namespace gls {
@@ -42,22 +51,39 @@ void set_luts(const uint64_t lut[][2], int ncells) {
 namespace {
 
 constexpr int CH = 128;                 // transitions per pin window
+constexpr int WIN = CH + 8;             // aligned lead (<= 3) + CH + sentinel, multiple of 4
 constexpr int PCAP = 256;               // carried (pending) transitions, > GLS_MAX_DELAY_SPREAD
 constexpr int QCAP = PCAP + 3 * CH;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr uint32_t EINF = 0xFFFFFFFFu;  // sentinel event; its time 2^30-1 exceeds every real time
 
-struct WarpSmem {
-    uint32_t A[3][CH];      // pin windows
-    uint32_t B[2 * CH];     // pins a+b merged (3-input cells)
-    uint16_t Binfo[2 * CH]; // source of B[i]: pin b flag (bit 15) | index in its window
-    uint32_t cand[3 * CH];  // per-lane stacks of scheduled transitions (t_r << 2 | v)
-    uint32_t Q[QCAP];       // carried + surviving transitions of the chunk
+struct __align__(16) WarpSmem {
+    uint32_t win[2][3][WIN];  // double-buffered pin windows
+    uint32_t B[2 * CH + 4];   // pins a+b merged (3-input cells), sentinel-terminated
+    uint16_t Binfo[2 * CH];   // source of B[i]: pin b flag (bit 15) | index in its window
+    uint32_t cand[3 * CH];    // per-lane stacks of scheduled transitions (t_r << 2 | v)
+    uint32_t Q[QCAP];         // carried + surviving transitions of the chunk
 };
 
-__device__ __forceinline__ uint32_t lut_eval(uint64_t lo, uint64_t hi, uint32_t st) {
-    uint64_t w = (st & 32u) ? hi : lo;
-    return (uint32_t)(w >> ((st & 31u) * 2u)) & 3u;
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
 }
 
 // Number of elements of L among the first d elements of merge(L, R), where an
@@ -65,19 +91,8 @@ __device__ __forceinline__ uint32_t lut_eval(uint64_t lo, uint64_t hi, uint32_t 
 __device__ __forceinline__ int corank(int d, const uint32_t *L, int nL, const uint32_t *R, int nR) {
     int lo = max(0, d - nR), hi = min(d, nL);
     while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if ((L[mid] >> 2) <= (R[d - mid - 1] >> 2)) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// count of a[0..n) with time <= T (a sorted by time)
-__device__ __forceinline__ int upper_count(const uint32_t *a, int n, uint32_t T) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if ((a[mid] >> 2) <= T) lo = mid + 1;
+        const int mid = (lo + hi) >> 1;
+        if (L[mid] <= (R[d - mid - 1] | 3u)) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -92,7 +107,6 @@ struct GateCtx {
     uint32_t len[3];
     uint32_t rise[3], fall[3], dx[3];
     uint32_t dmin;
-    int k;
     uint64_t lut_lo, lut_hi;
 };
 
@@ -100,16 +114,50 @@ __device__ __forceinline__ uint32_t pin_delay(const GateCtx &g, int p, uint32_t 
     return F == 1u ? g.rise[p] : (F == 0u ? g.fall[p] : g.dx[p]);
 }
 
+// Issue the asynchronous copies of every pin's next window into buffer b.
+// Window p covers transitions [cur[p], cur[p] + n[p]); the copy starts at the
+// 16-byte boundary below cur[p] (lead[p] <= 3 words) and ends at a multiple
+// of 4 words, which stays inside the net's slot (slots are padded to 4 words).
+template <int K>
+__device__ __forceinline__ bool issue_windows(WarpSmem &sm, int b, const GateCtx &g, const uint32_t *cur,
+                                              int *lead, int *n, int lane) {
+    bool any = false;
+#pragma unroll
+    for (int p = 0; p < K; p++) {
+        const int np = (int)min((uint32_t)CH, g.len[p] - cur[p]);
+        n[p] = np;
+        const uint32_t a = cur[p] & ~3u;
+        lead[p] = (int)(cur[p] - a);
+        if (np > 0) {
+            any = true;
+            const int vecs = (lead[p] + np + 3) >> 2;
+            const uint4 *src = reinterpret_cast<const uint4 *>(g.src[p] + a);
+            for (int v = lane; v < vecs; v += 32) cp_async16(&sm.win[b][p][4 * v], src + v);
+        }
+    }
+    cp_async_commit();
+    return any;
+}
+
+template <int K, bool DEP>
 __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem &sm, int lane) {
     GateCtx g;
-    g.k = gr.k;
     uint64_t bound = 0;
 #pragma unroll
     for (int p = 0; p < 3; p++) {
-        if (p < g.k) {
-            int32_t n = gr.fin[p];
-            g.src[p] = reinterpret_cast<const uint32_t *>(__ldg(reinterpret_cast<const unsigned long long *>(r.net_ptr) + n));
-            g.len[p] = __ldg(r.net_len + n);
+        if (p < K) {
+            const int32_t n = gr.fin[p];
+            uint64_t ptr;
+            uint32_t len;
+            if (DEP) {  // written during this launch: read through L2
+                ptr = __ldcg(reinterpret_cast<const unsigned long long *>(r.net_ptr) + n);
+                len = __ldcg(r.net_len + n);
+            } else {
+                ptr = __ldg(reinterpret_cast<const unsigned long long *>(r.net_ptr) + n);
+                len = __ldg(r.net_len + n);
+            }
+            g.src[p] = reinterpret_cast<const uint32_t *>(ptr);
+            g.len[p] = len;
             g.rise[p] = (uint32_t)gr.rise[p];
             g.fall[p] = (uint32_t)gr.fall[p];
             g.dx[p] = min(g.rise[p], g.fall[p]);
@@ -142,141 +190,176 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem &sm, int 
     }
     uint32_t *out = r.arena + base;
 
-    uint32_t carry = 0x2Au;           // pins a, b, c at X (2 | 2<<2 | 2<<4)
+    // 4-value tables: K == 1 uses f(a) with b = c = X (entries 40..43),
+    // K == 2 uses f(a, b) with c = X (entries 32..47), K == 3 all 64
+    const uint32_t lut1 = (uint32_t)(g.lut_hi >> 16) & 0xFFu;
+    const uint32_t lut2 = (uint32_t)g.lut_hi;
+
+    uint32_t carry = 0x2Au;           // pins a, b, c at X before the first transition
     uint32_t lastV = kVX;             // value of the last committed survivor
     uint32_t outCount = 0;
     int np = 0;                       // carried transitions in Q[0..np)
     uint32_t cur[3] = {0, 0, 0};
     const uint32_t lanemask_lt = (1u << lane) - 1u;
     bool failed = false;
+    int b = 0;
+    int lead[3] = {0, 0, 0}, n[3] = {0, 0, 0};
+    bool more = issue_windows<K>(sm, 0, g, cur, lead, n, lane);
 
-    for (;;) {
-        // ---- 1. windows and chunk cut ----
-        int n[3], m[3];
-        bool any = false;
-#pragma unroll
-        for (int p = 0; p < 3; p++) {
-            n[p] = (p < g.k) ? (int)min((uint32_t)CH, g.len[p] - cur[p]) : 0;
-            any |= n[p] > 0;
-        }
-        if (!any) break;
-#pragma unroll
-        for (int p = 0; p < 3; p++) {
-            const uint32_t *s = g.src[p] + cur[p];
-            for (int x = lane; x < n[p]; x += 32) sm.A[p][x] = __ldg(s + x);
-        }
+    while (more) {
+        cp_async_wait_all();
         __syncwarp();
+        const uint32_t *A[3];
+#pragma unroll
+        for (int p = 0; p < 3; p++) A[p] = &sm.win[b][p < K ? p : 0][p < K ? lead[p] : 0];
+
+        // ---- 1. chunk cut ----
         uint32_t Tend = kTimeInf;
 #pragma unroll
-        for (int p = 0; p < 3; p++)
-            if (n[p] > 0 && cur[p] + (uint32_t)n[p] < g.len[p]) Tend = min(Tend, sm.A[p][n[p] - 1] >> 2);
+        for (int p = 0; p < K; p++)
+            if (n[p] > 0 && cur[p] + (uint32_t)n[p] < g.len[p]) Tend = min(Tend, A[p][n[p] - 1] >> 2);
         const bool last = (Tend == kTimeInf);
+        int m[3] = {0, 0, 0};
 #pragma unroll
-        for (int p = 0; p < 3; p++) m[p] = last ? n[p] : upper_count(sm.A[p], n[p], Tend);
+        for (int p = 0; p < K; p++) {
+            if (last) { m[p] = n[p]; continue; }
+            int c = 0;
+            for (int x0 = 0; x0 < n[p]; x0 += 32) {
+                const int x = x0 + lane;
+                c += __popc(__ballot_sync(FULL, x < n[p] && (A[p][x] >> 2) <= Tend));
+            }
+            m[p] = c;
+        }
+        // start the copies of the next chunk before evaluating this one
+        uint32_t ncur[3] = {cur[0], cur[1], cur[2]};
+#pragma unroll
+        for (int p = 0; p < K; p++) ncur[p] += (uint32_t)m[p];
+        int nlead[3] = {0, 0, 0}, nn[3] = {0, 0, 0};
+        more = issue_windows<K>(sm, b ^ 1, g, ncur, nlead, nn, lane);
+        if (lane < K) {   // sentinels after the consumed part of every window
+            const int at = lane == 0 ? lead[0] + m[0] : (lane == 1 ? lead[1] + m[1] : lead[2] + m[2]);
+            sm.win[b][lane][at] = EINF;
+        }
+        __syncwarp();
 
-        // ---- 2. merge inputs: L (pin a, or a+b merged) and R (last pin) ----
-        const uint32_t *L = sm.A[0];
-        const uint32_t *R = sm.A[g.k - 1];
-        int nL = m[0], nR = (g.k >= 2) ? m[g.k - 1] : 0;
-        if (g.k == 3) {
+        // ---- 2./3. merge and per-lane walk (Algorithm 2 + local Eq. 1 stack) ----
+        const uint32_t *L = A[0];
+        const uint32_t *R = A[K - 1];
+        int nL = m[0], nR = K >= 2 ? m[K - 1] : 0;
+        if (K == 3) {
             const int M1 = m[0] + m[1];
             const int d0 = (lane * M1) >> 5, d1 = ((lane + 1) * M1) >> 5;
-            int i = corank(d0, sm.A[0], m[0], sm.A[1], m[1]), j = d0 - i;
-            uint32_t hl = i < m[0] ? sm.A[0][i] : EINF, hr = j < m[1] ? sm.A[1][j] : EINF;
+            int i = corank(d0, A[0], m[0], A[1], m[1]), j = d0 - i;
+            uint32_t hl = A[0][i], hr = A[1][j];
             for (int s = d0; s < d1; s++) {
-                if ((hl >> 2) <= (hr >> 2)) {
-                    sm.B[s] = hl; sm.Binfo[s] = (uint16_t)i; i++;
-                    hl = i < m[0] ? sm.A[0][i] : EINF;
-                } else {
-                    sm.B[s] = hr; sm.Binfo[s] = (uint16_t)(0x8000u | (uint32_t)j); j++;
-                    hr = j < m[1] ? sm.A[1][j] : EINF;
-                }
+                const bool tl = hl <= (hr | 3u);
+                sm.B[s] = tl ? hl : hr;
+                sm.Binfo[s] = tl ? (uint16_t)i : (uint16_t)(0x8000u | (uint32_t)j);
+                if (tl) { i++; hl = A[0][i]; } else { j++; hr = A[1][j]; }
             }
+            if (lane == 0) sm.B[M1] = EINF;
             __syncwarp();
-            L = sm.B; nL = M1;
+            L = sm.B;
+            nL = M1;
         }
-
-        // ---- 3. per-lane walk: Algorithm 2 with a local Eq. 1 stack ----
         const int M = nL + nR;
         const int d0 = (lane * M) >> 5, d1 = ((lane + 1) * M) >> 5;
-        int i = corank(d0, L, nL, R, nR), j = d0 - i;
-        int c0, c1, c2;   // transitions of pins a, b, c consumed before d0
-        if (g.k == 3) {
-            if (i == 0) { c0 = 0; c1 = 0; }
-            else {
-                uint32_t inf = sm.Binfo[i - 1], idx = inf & 0x7FFFu;
-                if (inf & 0x8000u) { c1 = (int)idx + 1; c0 = i - c1; }
-                else { c0 = (int)idx + 1; c1 = i - c0; }
-            }
-            c2 = j;
-        } else if (g.k == 2) { c0 = i; c1 = j; c2 = 0; }
-        else { c0 = i; c1 = 0; c2 = 0; }
-        const int cc[3] = {c0, c1, c2};
-        uint32_t st = carry, lt[3] = {kTimeInf, kTimeInf, kTimeInf};
-#pragma unroll
-        for (int p = 0; p < 3; p++)
-            if (p < g.k && cc[p] > 0) {
-                uint32_t e = sm.A[p][cc[p] - 1];
-                st = setpin(st, p, e & 3u);
-                lt[p] = e >> 2;
-            }
-        uint32_t hl = i < nL ? L[i] : EINF, hr = j < nR ? R[j] : EINF;
-        uint32_t Fprev = 0;
-        if (d0 < d1) {
-            // cell value just before the first timestamp of this share
-            uint32_t tf = min(hl >> 2, hr >> 2), sb = st;
-#pragma unroll
-            for (int p = 0; p < 3; p++)
-                if (p < g.k && cc[p] > 0 && lt[p] == tf) {
-                    uint32_t v = cc[p] >= 2 ? (sm.A[p][cc[p] - 2] & 3u) : ((carry >> (2 * p)) & 3u);
-                    sb = setpin(sb, p, v);
-                }
-            Fprev = lut_eval(g.lut_lo, g.lut_hi, sb);
-        }
         int top = d0;
         uint32_t trmax = 0;
-        for (int s = d0; s < d1; s++) {
-            uint32_t e;
-            int pin;
-            if ((hl >> 2) <= (hr >> 2)) {
-                e = hl;
-                pin = (g.k == 3) ? (int)(sm.Binfo[i] >> 15) : 0;
-                i++;
-                hl = i < nL ? L[i] : EINF;
-            } else {
-                e = hr;
-                pin = g.k - 1;
-                j++;
-                hr = j < nR ? R[j] : EINF;
+        if (K == 1) {
+            // one pin: every transition is its own timestamp
+            uint32_t Fprev = (lut1 >> (2 * (d0 > 0 ? (L[d0 - 1] & 3u) : (carry & 3u)))) & 3u;
+            for (int s = d0; s < d1; s++) {
+                const uint32_t e = L[s], t = e >> 2;
+                const uint32_t F = (lut1 >> (2 * (e & 3u))) & 3u;
+                if (F != Fprev) {
+                    const uint32_t tr = t + pin_delay(g, 0, F);
+                    trmax = max(trmax, tr);
+                    const uint32_t key = tr << 2;
+                    while (top > d0 && sm.cand[top - 1] >= key) top--;
+                    sm.cand[top++] = key | F;
+                }
+                Fprev = F;
             }
-            const uint32_t t = e >> 2;
-            st = setpin(st, pin, e & 3u);
-            lt[0] = pin == 0 ? t : lt[0];
-            lt[1] = pin == 1 ? t : lt[1];
-            lt[2] = pin == 2 ? t : lt[2];
-            if (min(hl >> 2, hr >> 2) == t) continue;   // more transitions at this time
-            const uint32_t F = lut_eval(g.lut_lo, g.lut_hi, st);
-            if (F != Fprev) {
-                uint32_t d = kTimeInf;
+        } else {
+            int i = corank(d0, L, nL, R, nR), j = d0 - i;
+            int c0, c1, c2;   // transitions of pins a, b, c consumed before d0
+            if (K == 3) {
+                if (i == 0) { c0 = 0; c1 = 0; }
+                else {
+                    const uint32_t inf = sm.Binfo[i - 1], idx = inf & 0x7FFFu;
+                    if (inf & 0x8000u) { c1 = (int)idx + 1; c0 = i - c1; }
+                    else { c0 = (int)idx + 1; c1 = i - c0; }
+                }
+                c2 = j;
+            } else { c0 = i; c1 = j; c2 = 0; }
+            const int cc[3] = {c0, c1, c2};
+            uint32_t st = carry, lt[3] = {kTimeInf, kTimeInf, kTimeInf};
 #pragma unroll
-                for (int p = 0; p < 3; p++)
-                    if (p < g.k && lt[p] == t) d = min(d, pin_delay(g, p, F));
-                const uint32_t tr = t + d;
-                trmax = max(trmax, tr);
-                const uint32_t key = tr << 2;
-                while (top > d0 && sm.cand[top - 1] >= key) top--;
-                sm.cand[top++] = key | F;
+            for (int p = 0; p < K; p++)
+                if (cc[p] > 0) {
+                    const uint32_t e = A[p][cc[p] - 1];
+                    st = setpin(st, p, e & 3u);
+                    lt[p] = e >> 2;
+                }
+            uint32_t hl = L[i], hr = R[j];
+            uint32_t Fprev = 0;
+            if (d0 < d1) {
+                // cell value just before the first timestamp of this share
+                const uint32_t tf = min(hl, hr) >> 2;
+                uint32_t sb = st;
+#pragma unroll
+                for (int p = 0; p < K; p++)
+                    if (cc[p] > 0 && lt[p] == tf) {
+                        const uint32_t v = cc[p] >= 2 ? (A[p][cc[p] - 2] & 3u) : ((carry >> (2 * p)) & 3u);
+                        sb = setpin(sb, p, v);
+                    }
+                Fprev = K == 3 ? (uint32_t)(((sb & 32u) ? g.lut_hi : g.lut_lo) >> (2 * (sb & 31u))) & 3u
+                               : (lut2 >> (2 * (sb & 15u))) & 3u;
             }
-            Fprev = F;
+            for (int s = d0; s < d1; s++) {
+                const bool tl = hl <= (hr | 3u);
+                const uint32_t e = tl ? hl : hr;
+                int pin;
+                if (tl) {
+                    pin = K == 3 ? (int)(sm.Binfo[i] >> 15) : 0;
+                    i++;
+                    hl = L[i];
+                } else {
+                    pin = K - 1;
+                    j++;
+                    hr = R[j];
+                }
+                const uint32_t t = e >> 2;
+                st = setpin(st, pin, e & 3u);
+                lt[0] = pin == 0 ? t : lt[0];
+                lt[1] = pin == 1 ? t : lt[1];
+                if (K == 3) lt[2] = pin == 2 ? t : lt[2];
+                if ((min(hl, hr) >> 2) == t) continue;   // more transitions at this time
+                const uint32_t F = K == 3 ? (uint32_t)(((st & 32u) ? g.lut_hi : g.lut_lo) >> (2 * (st & 31u))) & 3u
+                                          : (lut2 >> (2 * (st & 15u))) & 3u;
+                if (F != Fprev) {
+                    uint32_t d = kTimeInf;
+#pragma unroll
+                    for (int p = 0; p < K; p++)
+                        if (lt[p] == t) d = min(d, pin_delay(g, p, F));
+                    const uint32_t tr = t + d;
+                    trmax = max(trmax, tr);
+                    const uint32_t key = tr << 2;
+                    while (top > d0 && sm.cand[top - 1] >= key) top--;
+                    sm.cand[top++] = key | F;
+                }
+                Fprev = F;
+            }
         }
         if (trmax >= kTimeLimit) atomicOr(r.status, kStTimeRange);
 
         // ---- 4. Eq. 1 across lanes and against the carried transitions ----
-        uint32_t mn = top > d0 ? (sm.cand[d0] >> 2) : kTimeInf;
+        const uint32_t mn = top > d0 ? (sm.cand[d0] >> 2) : kTimeInf;
         uint32_t inc = mn;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_down_sync(FULL, inc, o);
+            const uint32_t y = __shfl_down_sync(FULL, inc, o);
             if (lane + o < 32) inc = min(inc, y);
         }
         uint32_t after = __shfl_down_sync(FULL, inc, 1);
@@ -284,16 +367,15 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem &sm, int 
         const uint32_t Mall = __shfl_sync(FULL, inc, 0);
         while (top > d0 && (sm.cand[top - 1] >> 2) >= after) top--;
         int npk = 0;
-        for (int b = 0; b < np; b += 32) {
-            int idx = b + lane;
-            bool f = idx < np && (sm.Q[idx] >> 2) < Mall;
-            npk += __popc(__ballot_sync(FULL, f));
+        for (int b0 = 0; b0 < np; b0 += 32) {
+            const int idx = b0 + lane;
+            npk += __popc(__ballot_sync(FULL, idx < np && (sm.Q[idx] >> 2) < Mall));
         }
         const uint32_t cnt = (uint32_t)(top - d0);
         uint32_t pre = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(FULL, pre, o);
+            const uint32_t y = __shfl_up_sync(FULL, pre, o);
             if (lane >= o) pre += y;
         }
         const int total = (int)__shfl_sync(FULL, pre, 31);
@@ -306,8 +388,8 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem &sm, int 
         // ---- 5. commit what no later transition can deny; drop repeats ----
         const uint32_t Tfin = last ? kTimeInf : Tend + 1u + g.dmin;
         int nf = 0;
-        for (int b = 0; b < nQ; b += 32) {
-            const int idx = b + lane;
+        for (int b0 = 0; b0 < nQ; b0 += 32) {
+            const int idx = b0 + lane;
             const uint32_t e = idx < nQ ? sm.Q[idx] : 0u;
             const bool fin = idx < nQ && (e >> 2) < Tfin;
             const uint32_t pv = idx == 0 ? lastV : (idx < nQ ? (sm.Q[idx - 1] & 3u) : 0u);
@@ -320,25 +402,35 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem &sm, int 
         if (nf > 0) lastV = sm.Q[nf - 1] & 3u;
         const int npn = nQ - nf;
         if (npn > PCAP) { failed = true; break; }
-        for (int b = 0; b < npn; b += 32) {
-            const int idx = b + lane;
+        for (int b0 = 0; b0 < npn; b0 += 32) {
+            const int idx = b0 + lane;
             const uint32_t e = idx < npn ? sm.Q[nf + idx] : 0u;
             __syncwarp();
             if (idx < npn) sm.Q[idx] = e;
         }
         np = npn;
 #pragma unroll
-        for (int p = 0; p < 3; p++)
-            if (m[p] > 0) {
-                carry = setpin(carry, p, sm.A[p][m[p] - 1] & 3u);
-                cur[p] += (uint32_t)m[p];
-            }
+        for (int p = 0; p < K; p++)
+            if (m[p] > 0) carry = setpin(carry, p, A[p][m[p] - 1] & 3u);
+#pragma unroll
+        for (int p = 0; p < 3; p++) { cur[p] = ncur[p]; lead[p] = nlead[p]; n[p] = nn[p]; }
+        b ^= 1;
         __syncwarp();
     }
+    if (failed) cp_async_wait_all();   // leave no copy in flight into this warp's buffers
     if (lane == 0) {
         if (failed) atomicOr(r.status, kStPendingOverflow);
         r.net_ptr[out_net] = reinterpret_cast<uint64_t>(out);
         r.net_len[out_net] = failed ? 0u : outCount;
+    }
+}
+
+template <bool DEP>
+__device__ __forceinline__ void eval_any(const GateRec &gr, const RunDev &r, WarpSmem &sm, int lane) {
+    switch (gr.k) {
+    case 1: eval_gate<1, DEP>(gr, r, sm, lane); break;
+    case 2: eval_gate<2, DEP>(gr, r, sm, lane); break;
+    default: eval_gate<3, DEP>(gr, r, sm, lane); break;
     }
 }
 
@@ -353,29 +445,78 @@ __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin,
         g = __shfl_sync(FULL, g, 0);
         if (g >= g_count) break;
         const GateRec gr = gates[g_begin + g];
-        eval_gate(gr, r, sm, lane);
+        eval_any<false>(gr, r, sm, lane);
         __syncwarp();
+    }
+}
+
+// Algorithm 1 without level barriers: gates are handed out in level order, so
+// every fanin gate of a handed-out gate was handed out earlier to a running
+// warp and the waits always end (the bound only guards against faults).
+__global__ void dependency_kernel(const GateRec *__restrict__ gates, int32_t n_gates, int32_t ctr_slot, RunDev r) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[warp];
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(r.level_ctr + ctr_slot, 1);
+        g = __shfl_sync(FULL, g, 0);
+        if (g >= n_gates) break;
+        const GateRec gr = gates[g];
+        bool ok = true;
+        if (lane < gr.k && gr.fin[lane] >= r.n_pi) {
+            const uint32_t *flag = r.done + (gr.fin[lane] - r.n_pi);
+            if (ld_acquire(flag) == 0u) {
+                const uint64_t t0 = globaltimer();
+                while (ld_acquire(flag) == 0u) {
+                    if (globaltimer() - t0 > r.wait_limit_ns) { ok = false; break; }
+                    __nanosleep(100);
+                }
+            }
+        }
+        ok = __all_sync(FULL, ok);
+        if (ok) {
+            eval_any<true>(gr, r, sm, lane);
+        } else if (lane == 0) {
+            atomicOr(r.status, kStTimeout);
+            r.net_ptr[gr.out_net] = 0;
+            r.net_len[gr.out_net] = 0;
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0 && g != r.withhold_gate) st_release(r.done + (gr.out_net - r.n_pi), 1u);
     }
 }
 
 }  // namespace
 
-size_t level_smem_bytes(int warps_per_cta) { return sizeof(WarpSmem) * (size_t)warps_per_cta; }
+size_t gate_smem_bytes(int warps_per_cta) { return sizeof(WarpSmem) * (size_t)warps_per_cta; }
 
-int level_max_ctas_per_sm(int warps_per_cta) {
-    int n = 0;
-    size_t sm = level_smem_bytes(warps_per_cta);
+int gate_max_ctas_per_sm(int warps_per_cta) {
+    const size_t sm = gate_smem_bytes(warps_per_cta);
     cudaFuncSetAttribute(level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, level_kernel, warps_per_cta * 32, sm);
-    return n;
+    cudaFuncSetAttribute(dependency_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, level_kernel, warps_per_cta * 32, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dependency_kernel, warps_per_cta * 32, sm);
+    return a < b ? a : b;
 }
 
 cudaError_t launch_level(const GateRec *d_gates, int32_t g_begin, int32_t g_count, int32_t level,
                          const RunDev &r, const LevelCfg &cfg, cudaStream_t s) {
     if (g_count <= 0) return cudaSuccess;
-    int ctas = min(cfg.ctas, (g_count + cfg.warps_per_cta - 1) / cfg.warps_per_cta);
-    size_t sm = level_smem_bytes(cfg.warps_per_cta);
-    level_kernel<<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
+    const int ctas = min(cfg.ctas, (g_count + cfg.warps_per_cta - 1) / cfg.warps_per_cta);
+    level_kernel<<<ctas, cfg.warps_per_cta * 32, gate_smem_bytes(cfg.warps_per_cta), s>>>(d_gates, g_begin,
+                                                                                          g_count, level, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dependency(const GateRec *d_gates, int32_t n_gates, int32_t ctr_slot, const RunDev &r,
+                              const LevelCfg &cfg, cudaStream_t s) {
+    if (n_gates <= 0) return cudaSuccess;
+    const int ctas = min(cfg.ctas, (n_gates + cfg.warps_per_cta - 1) / cfg.warps_per_cta);
+    dependency_kernel<<<ctas, cfg.warps_per_cta * 32, gate_smem_bytes(cfg.warps_per_cta), s>>>(d_gates, n_gates,
+                                                                                               ctr_slot, r);
     return cudaGetLastError();
 }
 

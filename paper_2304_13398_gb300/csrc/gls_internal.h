@@ -11,7 +11,7 @@ namespace gls {
 // time field of the all-ones sentinel word.  Values: 0, 1, 2 = X, 3 = Z.
 constexpr uint32_t kVX = 2;
 constexpr uint32_t kTimeLimit = (1u << 30) - 1u;   // exclusive
-constexpr uint32_t kTimeInf = 0xFFFFFFFFu;     // "no more transitions"
+constexpr uint32_t kTimeInf = 0xFFFFFFFFu;         // "no more transitions"
 
 // Device gate record, gates stored in level order (48 bytes, 16-byte aligned).
 // fin[] are internal net ids: 0..n_pi-1 primary inputs, n_pi+i internal gate i.
@@ -29,7 +29,8 @@ static_assert(sizeof(GateRec) == 48, "GateRec layout");
 enum : uint32_t {
     kStArenaOverflow = 1u,    // output arena too small
     kStPendingOverflow = 2u,  // a cell's pending transitions exceeded the buffer
-    kStTimeRange = 4u,        // a computed time reached 2^30
+    kStTimeRange = 4u,        // a computed time reached 2^30 - 1
+    kStTimeout = 8u,          // a bounded wait for a fanin gave up
 };
 
 // Per-run device state.
@@ -40,34 +41,47 @@ struct RunDev {
     uint64_t arena_cap;       // capacity in transitions
     unsigned long long *arena_top;  // bump pointer (transitions), counts demand past cap
     uint32_t *status;         // kSt* bits
-    int32_t *level_ctr;       // [depth] work counters, zeroed per run
+    int32_t *level_ctr;       // [depth + 1] work counters, zeroed per run (last: dependency mode)
+    uint32_t *done;           // [G] per-gate completion flags (dependency mode), zeroed per run
+    int32_t n_pi;
+    int32_t n_gates;
+    uint64_t wait_limit_ns;   // bound on one wait for a fanin (dependency mode)
+    int32_t withhold_gate;    // test hook: this gate never publishes its flag (-1: none)
 };
 
-// Level kernel configuration (chosen per launch).
+// Launch configuration of the gate kernels.
 struct LevelCfg {
     int warps_per_cta;
-    int ctas;
+    int ctas;                 // resident CTAs on the whole GPU
 };
 
 // Stimulus device layout: PI i's packed transitions start at word
-// stim_base(off[i], i) = (off[i] + 3 i + 3) & ~3 (16-byte aligned, disjoint).
+// stim_slot(off[i], i) = (off[i] + 3 i + 3) & ~3 (16-byte aligned, disjoint,
+// and every read rounded up to a multiple of 4 words stays inside the buffer
+// of stim_words(E, n_pi) words).
 __host__ __device__ inline uint64_t stim_slot(int64_t off_i, int64_t i) {
     return (uint64_t)((off_i + 3 * i + 3) & ~(int64_t)3);
 }
 __host__ __device__ inline uint64_t stim_words(int64_t n_events, int64_t n_pi) {
-    return (uint64_t)(n_events + 3 * n_pi + 4);
+    return (uint64_t)(n_events + 3 * n_pi + 8);
 }
 
-// ---- launch wrappers (gls_kernels.cu) ----
+// ---- launch wrappers ----
 void set_luts(const uint64_t lut[][2], int ncells);
-cudaError_t launch_pack_stimulus(const int64_t *d_off, const int32_t *d_t, const uint8_t *d_v, int32_t n_pi,
-                                 uint32_t *d_packed, uint32_t *d_status, cudaStream_t s);
-cudaError_t launch_run_init(const int64_t *d_stim_off, const uint32_t *d_stim_packed, int32_t n_pi,
-                            const RunDev &r, int32_t depth, cudaStream_t s);
+size_t gate_smem_bytes(int warps_per_cta);
+int gate_max_ctas_per_sm(int warps_per_cta);
+// one level: gates [g_begin, g_begin + g_count) of the level-ordered array
 cudaError_t launch_level(const GateRec *d_gates, int32_t g_begin, int32_t g_count, int32_t level,
                          const RunDev &r, const LevelCfg &cfg, cudaStream_t s);
-size_t level_smem_bytes(int warps_per_cta);
-int level_max_ctas_per_sm(int warps_per_cta);
+// all gates in one persistent launch, each gate started once its fanin gates
+// are done (Algorithm 1 scheduling without level barriers)
+cudaError_t launch_dependency(const GateRec *d_gates, int32_t n_gates, int32_t ctr_slot, const RunDev &r,
+                              const LevelCfg &cfg, cudaStream_t s);
+
+cudaError_t launch_pack_stimulus(const int64_t *d_off, const int32_t *d_t, const uint8_t *d_v, int32_t n_pi,
+                                 uint32_t *d_packed, uint32_t *d_status, cudaStream_t s);
+cudaError_t launch_run_init(const int64_t *d_stim_off, const uint32_t *d_stim_packed, const RunDev &r,
+                            int32_t n_ctr, cudaStream_t s);
 cudaError_t launch_gather_lengths(const uint32_t *d_net_len, const int32_t *d_ext2int, int64_t n,
                                   int64_t *d_off, cudaStream_t s);
 cudaError_t launch_exclusive_scan_i64(int64_t *d_data, int64_t n, int64_t *d_tmp, size_t tmp_elems,

@@ -39,17 +39,18 @@ __global__ void pack_stimulus_kernel(const int64_t *__restrict__ off, const int3
 }
 
 // PI net descriptors point into the packed stimulus; everything a run
-// accumulates is reset.
-__global__ void run_init_kernel(const int64_t *__restrict__ off, const uint32_t *packed, int32_t n_pi, RunDev r,
-                                int32_t depth) {
+// accumulates (counters, status, completion flags) is reset.
+__global__ void run_init_kernel(const int64_t *__restrict__ off, const uint32_t *packed, RunDev r, int32_t n_ctr) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = tid; i < n_pi; i += stride) {
+    for (int64_t i = tid; i < r.n_pi; i += stride) {
         const int64_t a = off[i];
         r.net_ptr[i] = reinterpret_cast<uint64_t>(packed + stim_slot(a, i));
         r.net_len[i] = (uint32_t)(off[i + 1] - a);
     }
-    for (int64_t i = tid; i < depth; i += stride) r.level_ctr[i] = 0;
+    for (int64_t i = tid; i < n_ctr; i += stride) r.level_ctr[i] = 0;
+    if (r.done)
+        for (int64_t i = tid; i < r.n_gates; i += stride) r.done[i] = 0u;
     if (tid == 0) { *r.arena_top = 0; *r.status = 0; }
 }
 
@@ -153,10 +154,12 @@ cudaError_t launch_pack_stimulus(const int64_t *d_off, const int32_t *d_t, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_run_init(const int64_t *d_stim_off, const uint32_t *d_stim_packed, int32_t n_pi,
-                            const RunDev &r, int32_t depth, cudaStream_t s) {
-    run_init_kernel<<<grid_for((int64_t)n_pi > depth ? n_pi : depth, 256), 256, 0, s>>>(
-        d_stim_off, d_stim_packed, n_pi, r, depth);
+cudaError_t launch_run_init(const int64_t *d_stim_off, const uint32_t *d_stim_packed, const RunDev &r,
+                            int32_t n_ctr, cudaStream_t s) {
+    int64_t work = r.n_pi;
+    if (r.done && r.n_gates > work) work = r.n_gates;
+    if (n_ctr > work) work = n_ctr;
+    run_init_kernel<<<grid_for(work, 256), 256, 0, s>>>(d_stim_off, d_stim_packed, r, n_ctr);
     return cudaGetLastError();
 }
 

@@ -44,8 +44,12 @@ SIGNATURES = [
     ("gls_run_stats", ctypes.c_int, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]),
     ("gls_read_waveform", ctypes.c_int, [P, i32, i32, P, P, i64, ctypes.POINTER(i64)]),
     ("gls_read_all", ctypes.c_int, [P, i32, P, P, i64]),
+    ("gls_set_option", ctypes.c_int, [P, ctypes.c_int, i64]),
     ("gls_release", ctypes.c_int, [P, i32]),
 ]
+GLS_OPT_SCHEDULE, GLS_OPT_WARPS_PER_CTA, GLS_OPT_WAIT_LIMIT_MS, GLS_OPT_TEST_WITHHOLD_GATE = 1, 2, 3, 4
+GLS_SCHEDULE_LEVELS, GLS_SCHEDULE_DEPENDENCY = 0, 1
+SCHEDULES = {"levels": GLS_SCHEDULE_LEVELS, "dependency": GLS_SCHEDULE_DEPENDENCY}
 
 _lib = None
 
@@ -155,6 +159,14 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+    def set_option(self, option: int, value: int):
+        self._ck(self.lib.gls_set_option(self.h, option, value))
+
+    def set_schedule(self, name: str):
+        """'levels' (one launch per DAG level) or 'dependency' (one persistent
+        launch, gates start when their fanins are done)."""
+        self.set_option(GLS_OPT_SCHEDULE, SCHEDULES[name])
 
     def load_netlist(self, nl) -> int:
         typ, fo, fn = _c(nl.type, np.uint8), _c(nl.fanin_off, np.int32), _c(nl.fanin_net, np.int32)

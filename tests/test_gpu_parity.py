@@ -13,9 +13,10 @@ pytestmark = pytest.mark.gpu
 X, Z = 2, 3
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=["dependency", "levels"])
+def ctx(request):
     c = gls.Context(0)
+    c.set_schedule(request.param)
     yield c
     c.close()
 
@@ -217,3 +218,26 @@ def test_error_paths(ctx):
         ctx.simulate(12345, sid)
     with pytest.raises(gls.GlsError):
         ctx.release(nid)          # run still uses it
+
+
+def test_bounded_wait_reports_timeout():
+    # a gate that never signals completion: its readers give up after the
+    # wait limit, the kernel finishes and the host reads GLS_ETIMEOUT
+    E = gls.gls
+    w = synth.make_workload("tiny200", seed=3)
+    with gls.Context(0) as c:
+        c.set_schedule("dependency")
+        c.set_option(E.GLS_OPT_WAIT_LIMIT_MS, 50)
+        c.set_option(E.GLS_OPT_TEST_WITHHOLD_GATE, 0)   # first gate of level 1 has readers
+        nid = c.load_netlist(w.netlist)
+        sid = c.load_stimulus(w.stimulus)
+        rid = c.simulate(nid, sid)
+        rc, _, _ = c.run_stats_raw(rid)
+        assert rc == E.GLS_ETIMEOUT
+        # the context stays usable: the same netlist without the hook is exact
+        c.set_option(E.GLS_OPT_TEST_WITHHOLD_GATE, -1)
+        rid = c.simulate(nid, sid)
+        c.run_stats(rid)
+        off, packed = c.read_all(rid)
+        t, v = gls.unpack(packed)
+        assert_same(oracle.sim_event(w.netlist, w.stimulus), off, t, v, "after timeout")
