@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--arena-words", type=int, default=0, help="event arena size (0: size from a first run)")
     ap.add_argument("--schedule", default="dependency", choices=["dependency", "levels"])
     ap.add_argument("--warps-per-cta", type=int, default=0)
+    ap.add_argument("--kernel", default="windowed", choices=["windowed", "segmented"])
+    ap.add_argument("--segment", type=int, default=0, help="segmented kernel: transitions per lane segment")
     return ap.parse_args()
 
 
@@ -258,6 +260,9 @@ def run_own(a):
     nl, st = w.netlist, w.stimulus
     ctx = gls.Context(local)
     ctx.set_schedule(a.schedule)
+    ctx.set_kernel(a.kernel)
+    if a.segment:
+        ctx.set_option(gls.gls.GLS_OPT_SEGMENT, a.segment)
     if a.warps_per_cta:
         ctx.set_option(gls.gls.GLS_OPT_WARPS_PER_CTA, a.warps_per_cta)
     stream = torch.cuda.Stream()
@@ -352,7 +357,7 @@ def run_own(a):
     cfg = describe(a.workload, w)
     cfg.update({"output_transitions_per_step": e_out, "arena_words": int(arena) if arena else "default",
                 "l2_policy": "inputs larger than L2 (stimulus and intermediate waveforms >> 129 MB)",
-                "parallelism": f"replicas{world}" if world > 1 else "single", "schedule": a.schedule})
+                "parallelism": f"replicas{world}" if world > 1 else "single", "schedule": a.schedule, "kernel": a.kernel})
     launches_per_step = 1 + (1 if a.schedule == "dependency" else int(w.recipe["net"]["depth"]))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": max(a.warmup, 3), "ms_per_step": ms, "sim_time_ms": ms, "higher_is_better": True,

@@ -200,10 +200,20 @@ typedef enum gls_option {
     GLS_OPT_SCHEDULE = 1,       /* GLS_SCHEDULE_LEVELS or GLS_SCHEDULE_DEPENDENCY (default)  */
     GLS_OPT_WARPS_PER_CTA = 2,  /* warps per CTA of the gate kernels, 1..32 (default 4)        */
     GLS_OPT_WAIT_LIMIT_MS = 3,  /* bound on one device wait for a fanin gate (default 10000)    */
-    GLS_OPT_TEST_WITHHOLD_GATE = 4  /* test hook for the bounded wait: the gate at this level-order
+    GLS_OPT_TEST_WITHHOLD_GATE = 4, /* test hook for the bounded wait: the gate at this level-order
                                        position never signals completion, so its readers wait out
                                        the limit and the run reports GLS_ETIMEOUT (-1 = off)     */
+    GLS_OPT_KERNEL = 5,         /* GLS_KERNEL_WINDOWED (default) or GLS_KERNEL_SEGMENTED        */
+    GLS_OPT_SEGMENT = 6         /* segmented kernel: input transitions per lane segment, >= 1
+                                   (default 32); a gate uses min(32, ceil(inputs / this)) lanes */
 } gls_option;
+
+/* Gate kernel variants; both compute the same waveforms.
+   SEGMENTED: each lane of a warp evaluates one time segment of the gate
+   sequentially and the segments are reconciled once per gate.
+   WINDOWED: the warp streams shared-memory windows of all pins and merges,
+   evaluates and filters each window cooperatively. */
+enum { GLS_KERNEL_SEGMENTED = 0, GLS_KERNEL_WINDOWED = 1 };
 
 /* Schedules of the gate evaluation (Sec. 4.1).
    LEVELS: one kernel launch per DAG level (the topological-layer partition

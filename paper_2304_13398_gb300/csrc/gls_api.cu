@@ -247,10 +247,11 @@ struct gls_ctx {
     uint64_t budget = 0, used = 0;
     cudaStream_t stream = nullptr, cap_stream = nullptr;
     int sm_count = 0;
-    LevelCfg cfg{8, 0};
+    LevelCfg cfg{4, 0, kVariantWindowed};
     int schedule = GLS_SCHEDULE_DEPENDENCY;
     uint64_t wait_limit_ns = 10ull * 1000 * 1000 * 1000;
     int32_t withhold_gate = -1;
+    uint32_t seg_target = 32;
     int32_t next_id = 1;
     std::unordered_map<int32_t, std::unique_ptr<NetlistObj>> netlists;
     std::unordered_map<int32_t, std::unique_ptr<StimObj>> stims;
@@ -386,10 +387,11 @@ int build_run_graph(gls_ctx *c, RunObj *r, NetlistObj *n, StimObj *s) {
     return GLS_OK;
 }
 
-int apply_launch_cfg(gls_ctx *c, int warps_per_cta) {
-    const int per_sm = gate_max_ctas_per_sm(warps_per_cta);
+int apply_launch_cfg(gls_ctx *c, int variant, int warps_per_cta) {
+    const int per_sm = gate_max_ctas_per_sm(variant, warps_per_cta);
     CK(cudaGetLastError());
     if (per_sm < 1) return fail(GLS_EINVAL, "%d warps per CTA do not fit on an SM", warps_per_cta);
+    c->cfg.variant = variant;
     c->cfg.warps_per_cta = warps_per_cta;
     c->cfg.ctas = per_sm * c->sm_count;
     return GLS_OK;
@@ -450,7 +452,7 @@ int gls_create(gls_ctx **out, int device, uint64_t hbm_budget_bytes) {
         build_luts(lut);
         set_luts(lut, GLS_NCELLS);
         CK(cudaGetLastError());
-        int rc = apply_launch_cfg(c.get(), 4);
+        int rc = apply_launch_cfg(c.get(), kVariantWindowed, 4);
         if (rc) return rc;
         rc = dalloc_n(c.get(), &c->d_status, 4);
         if (rc) return rc;
@@ -594,10 +596,12 @@ int gls_simulate(gls_ctx *c, int32_t netlist_id, int32_t stim_id, int64_t arena_
         r->dev.n_gates = n->n_gates;
         r->dev.wait_limit_ns = c->wait_limit_ns;
         r->dev.withhold_gate = c->withhold_gate;
+        r->dev.seg_target = c->seg_target;
         r->schedule = c->schedule;
         rc = dalloc_n(c, &r->dev.net_ptr, (size_t)std::max<int64_t>(N, 1));
         if (!rc) rc = dalloc_n(c, &r->dev.net_len, (size_t)std::max<int64_t>(N, 1));
-        if (!rc) rc = dalloc_n(c, &r->dev.arena, (size_t)std::max<int64_t>(arena_events, 4));
+        // padded by one slot line: readers round a waveform's end up to 4 words
+        if (!rc) rc = dalloc_n(c, &r->dev.arena, (size_t)arena_events + 2 * kSlotAlign);
         if (!rc) rc = dalloc_n(c, &r->dev.arena_top, 1);
         if (!rc) rc = dalloc_n(c, &r->dev.status, 1);
         if (!rc) rc = dalloc_n(c, &r->dev.level_ctr, (size_t)n->lv.depth + 1);
@@ -747,10 +751,19 @@ int gls_set_option(gls_ctx *c, int option, int64_t value) {
         return GLS_OK;
     case GLS_OPT_WARPS_PER_CTA:
         if (value < 1 || value > 32) return fail(GLS_EINVAL, "warps per CTA must be in [1, 32]");
-        return apply_launch_cfg(c, (int)value);
+        return apply_launch_cfg(c, c->cfg.variant, (int)value);
     case GLS_OPT_WAIT_LIMIT_MS:
         if (value < 1) return fail(GLS_EINVAL, "wait limit must be >= 1 ms");
         c->wait_limit_ns = (uint64_t)value * 1000000ull;
+        return GLS_OK;
+    case GLS_OPT_KERNEL:
+        if (value != GLS_KERNEL_SEGMENTED && value != GLS_KERNEL_WINDOWED)
+            return fail(GLS_EINVAL, "unknown kernel variant %lld", (long long)value);
+        return apply_launch_cfg(c, value == GLS_KERNEL_SEGMENTED ? kVariantSegmented : kVariantWindowed,
+                                c->cfg.warps_per_cta);
+    case GLS_OPT_SEGMENT:
+        if (value < 1 || value > (1 << 20)) return fail(GLS_EINVAL, "segment target must be in [1, 2^20]");
+        c->seg_target = (uint32_t)value;
         return GLS_OK;
     case GLS_OPT_TEST_WITHHOLD_GATE:
         if (value < -1 || value > INT32_MAX) return fail(GLS_EINVAL, "gate index out of range");

@@ -74,11 +74,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+    asm volatile("st.release.gpu.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
@@ -178,7 +178,7 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem &sm, int 
         return;
     }
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(r.arena_top, (unsigned long long)((bound + 3) & ~3ull));
+    if (lane == 0) base = atomicAdd(r.arena_top, (unsigned long long)((bound + kSlotAlign - 1) & ~(uint64_t)(kSlotAlign - 1)));
     base = __shfl_sync(FULL, base, 0);
     if (base + bound > r.arena_cap) {
         if (lane == 0) {
@@ -426,7 +426,7 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem &sm, int 
 }
 
 template <bool DEP>
-__device__ __forceinline__ void eval_any(const GateRec &gr, const RunDev &r, WarpSmem &sm, int lane) {
+__device__ __forceinline__ void eval_windowed(const GateRec &gr, const RunDev &r, WarpSmem &sm, int lane) {
     switch (gr.k) {
     case 1: eval_gate<1, DEP>(gr, r, sm, lane); break;
     case 2: eval_gate<2, DEP>(gr, r, sm, lane); break;
@@ -434,18 +434,316 @@ __device__ __forceinline__ void eval_any(const GateRec &gr, const RunDev &r, War
     }
 }
 
+// ===========================================================================
+// Segmented variant: the lanes of the warp split one gate's input timeline
+// into consecutive segments [T_l, T_l+1) of about equal transition counts
+// (quantiles of the longest fanin waveform).  Each lane runs Algorithm 2 and
+// the sequential Eq. 1 stack (deny every scheduled transition with
+// t_r' >= t_r, drop a transition equal to the one below it) on its own
+// segment, streaming its inputs with 16-byte loads and keeping the stack in
+// its private part of the gate's output slot.  Segments interact only
+// through Eq. 1 across a boundary, resolved once per gate:
+//   - a lane's stack tail is denied by any transition of a later segment with
+//     a smaller or equal t_r: pop while t_r >= (suffix minimum of the later
+//     lanes' smallest candidate t_r);
+//   - the bottom of each lane's stack was pushed onto an empty local stack, so
+//     whether it repeats the value before it is decided against the last
+//     surviving transition of the nearest earlier non-empty lane (X if none);
+// and a warp-wide copy packs the lanes' stacks into one contiguous waveform.
+// There is no per-chunk work and no shared memory.
+namespace seg {
+
+
+template <bool DEP>
+__device__ __forceinline__ uint4 ld16(const uint4 *p) {
+    if (DEP) {   // produced during this launch: coherent load after the acquire
+        uint4 v;
+        asm volatile("ld.v4.u32 {%0,%1,%2,%3}, [%4];\n"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+        return v;
+    }
+    return __ldg(p);
+}
+template <bool DEP>
+__device__ __forceinline__ uint32_t ld4(const uint32_t *p) {
+    if (DEP) {
+        uint32_t v;
+        asm volatile("ld.u32 %0, [%1];\n" : "=r"(v) : "l"(p));
+        return v;
+    }
+    return __ldg(p);
+}
+__device__ __forceinline__ uint32_t pick(const uint4 &b, uint32_t i) {
+    return i == 0 ? b.x : (i == 1 ? b.y : (i == 2 ? b.z : b.w));
+}
+
+// Transitions [s, e) of one pin, read 16 bytes at a time through L1; the
+// 128-byte line after the current one is prefetched into L1 when the stream
+// enters a line.  Reads and prefetches stay inside the net's slot: they start
+// at the 16-byte boundary below s and never pass the multiple of 4 words at
+// or above e (slots are padded to whole lines).
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+    asm volatile("prefetch.L1 [%0];\n" ::"l"(p));
+}
+template <bool DEP>
+struct PinStream {
+    const uint32_t *base;
+    uint32_t idx, end, head;   // current index, end index, current transition (EINF at the end)
+    uint4 buf;
+    __device__ __forceinline__ void init(const uint32_t *b, uint32_t s, uint32_t e) {
+        base = b;
+        idx = s;
+        end = e;
+        head = EINF;
+        if (s >= e) return;
+        const uint32_t a = s & ~3u;
+        buf = ld16<DEP>(reinterpret_cast<const uint4 *>(b + a));
+        const uint32_t nl = (a & ~31u) + 32;   // next line
+        if (nl < e) prefetch_l1(b + nl);
+        head = pick(buf, s & 3u);
+    }
+    __device__ __forceinline__ void advance() {
+        if (++idx >= end) { head = EINF; return; }
+        if ((idx & 3u) == 0) {
+            buf = ld16<DEP>(reinterpret_cast<const uint4 *>(base + idx));
+            if ((idx & 31u) == 0 && idx + 32 < end) prefetch_l1(base + idx + 32);
+        }
+        head = pick(buf, idx & 3u);
+    }
+};
+
+// first index of a[0..n) with time >= T
+template <bool DEP>
+__device__ __forceinline__ uint32_t lower_bound_t(const uint32_t *a, uint32_t n, uint32_t T) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((ld4<DEP>(a + mid) >> 2) < T) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int K, bool DEP>
+__device__ void eval_gate_seg(const GateRec &gr, const RunDev &r, int lane) {
+    const uint32_t *src[3];
+    uint32_t len[3], rise[3], fall[3];
+    uint64_t bound = 0;
+#pragma unroll
+    for (int p = 0; p < K; p++) {
+        const int32_t n = gr.fin[p];
+        uint64_t ptr;
+        if (DEP) {
+            ptr = __ldcg(reinterpret_cast<const unsigned long long *>(r.net_ptr) + n);
+            len[p] = __ldcg(r.net_len + n);
+        } else {
+            ptr = __ldg(reinterpret_cast<const unsigned long long *>(r.net_ptr) + n);
+            len[p] = __ldg(r.net_len + n);
+        }
+        src[p] = reinterpret_cast<const uint32_t *>(ptr);
+        rise[p] = (uint32_t)gr.rise[p];
+        fall[p] = (uint32_t)gr.fall[p];
+        bound += len[p];
+    }
+    const uint32_t out_net = gr.out_net;
+    if (bound == 0) {   // no input transition: the output stays X
+        if (lane == 0) { r.net_ptr[out_net] = 0; r.net_len[out_net] = 0; }
+        return;
+    }
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(r.arena_top, (unsigned long long)((bound + kSlotAlign - 1) & ~(uint64_t)(kSlotAlign - 1)));
+    base = __shfl_sync(FULL, base, 0);
+    if (base + bound > r.arena_cap) {
+        if (lane == 0) {
+            atomicOr(r.status, kStArenaOverflow);
+            r.net_ptr[out_net] = 0;
+            r.net_len[out_net] = 0;
+        }
+        return;
+    }
+    uint32_t *const slot = r.arena + base;
+    const uint64_t lut_lo = c_lut[gr.type][0], lut_hi = c_lut[gr.type][1];
+
+    // ---- segments: lane l takes input times [T_l, T_l+1) ----
+    const uint32_t S = (uint32_t)min((uint64_t)32, (bound + r.seg_target - 1) / r.seg_target);
+    int pilot = 0;
+#pragma unroll
+    for (int p = 1; p < K; p++)
+        if (len[p] > len[pilot]) pilot = p;
+    uint32_t lp = len[0];
+    const uint32_t *ps = src[0];
+#pragma unroll
+    for (int p = 1; p < K; p++)
+        if (p == pilot) { lp = len[p]; ps = src[p]; }
+    uint32_t sidx[3];
+    if ((uint32_t)lane < S && lane > 0) {
+        const uint32_t q = (uint32_t)(((uint64_t)lane * lp) / S);
+        const uint32_t T = ld4<DEP>(ps + q) >> 2;
+#pragma unroll
+        for (int p = 0; p < K; p++) sidx[p] = (p == pilot) ? q : lower_bound_t<DEP>(src[p], len[p], T);
+    } else {
+#pragma unroll
+        for (int p = 0; p < K; p++) sidx[p] = lane == 0 ? 0u : len[p];
+    }
+    uint32_t eidx[3], nseg = 0;
+#pragma unroll
+    for (int p = 0; p < K; p++) {
+        eidx[p] = __shfl_down_sync(FULL, sidx[p], 1);
+        if (lane == 31) eidx[p] = len[p];
+        nseg += eidx[p] - sidx[p];
+    }
+    uint32_t segoff = nseg;   // exclusive prefix of segment sizes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, segoff, o);
+        if (lane >= o) segoff += y;
+    }
+    segoff -= nseg;
+    uint32_t *const out = slot + segoff;
+
+    // ---- per-lane Algorithm 2 + Eq. 1 stack ----
+    uint32_t st = 0x2Au;
+    PinStream<DEP> in[K];
+#pragma unroll
+    for (int p = 0; p < K; p++) {
+        // value of pin p just before the segment (X before its first transition)
+        st = setpin(st, p, sidx[p] > 0 ? (ld4<DEP>(src[p] + sidx[p] - 1) & 3u) : kVX);
+        in[p].init(src[p], sidx[p], eidx[p]);
+    }
+    auto lut = [&](uint32_t x) -> uint32_t {
+        return (uint32_t)(((x & 32u) ? lut_hi : lut_lo) >> (2 * (x & 31u))) & 3u;
+    };
+    uint32_t Fprev = lut(st);
+    uint32_t pos = 0, top = 0, top2 = 0, mintr = kTimeInf, trmax = 0;   // top, top2: out[pos-1], out[pos-2]
+    for (;;) {
+        uint32_t h = in[0].head;
+#pragma unroll
+        for (int p = 1; p < K; p++) h = min(h, in[p].head);
+        if (h == EINF) break;
+        const uint32_t t = h >> 2;
+        uint32_t ch = 0;
+#pragma unroll
+        for (int p = 0; p < K; p++) {
+            if ((in[p].head >> 2) == t) {
+                st = setpin(st, p, in[p].head & 3u);
+                ch |= 1u << p;
+                in[p].advance();
+            }
+        }
+        const uint32_t F = lut(st);
+        if (F != Fprev) {
+            uint32_t d = kTimeInf;
+#pragma unroll
+            for (int p = 0; p < K; p++)
+                if (ch & (1u << p)) d = min(d, F == 1u ? rise[p] : (F == 0u ? fall[p] : min(rise[p], fall[p])));
+            const uint32_t tr = t + d;
+            trmax = max(trmax, tr);
+            mintr = min(mintr, tr);
+            const uint32_t key = tr << 2;
+            while (pos > 0 && top >= key) {   // Eq. 1: deny t_r' >= t_r
+                pos--;
+                top = top2;
+                top2 = pos >= 2 ? out[pos - 2] : 0u;
+            }
+            if (pos == 0 || (top & 3u) != F) {   // a repeat of the value below is dropped
+                top2 = top;
+                top = key | F;
+                out[pos++] = top;
+            }
+        }
+        Fprev = F;
+    }
+    if (trmax >= kTimeLimit) atomicOr(r.status, kStTimeRange);
+
+    // ---- Eq. 1 across segments ----
+    uint32_t inc = mintr;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_down_sync(FULL, inc, o);
+        if (lane + o < 32) inc = min(inc, y);
+    }
+    uint32_t after = __shfl_down_sync(FULL, inc, 1);
+    if (lane == 31) after = kTimeInf;
+    while (pos > 0 && (top >> 2) >= after) {
+        pos--;
+        top = top2;
+        top2 = pos >= 2 ? out[pos - 2] : 0u;
+    }
+    // value before each lane's bottom: last survivor of the nearest earlier non-empty lane
+    bool hv = pos > 0;
+    uint32_t vv = top & 3u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const bool h2 = __shfl_up_sync(FULL, (int)hv, o);
+        const uint32_t v2 = __shfl_up_sync(FULL, vv, o);
+        if (lane >= o && !hv) { hv = h2; vv = v2; }
+    }
+    bool ph = __shfl_up_sync(FULL, (int)hv, 1);
+    uint32_t pv = __shfl_up_sync(FULL, vv, 1);
+    if (lane == 0) { ph = false; }
+    const uint32_t before = ph ? pv : kVX;
+    const uint32_t drop = (pos > 0 && (out[0] & 3u) == before) ? 1u : 0u;
+    const uint32_t flen = pos - drop;
+    uint32_t foff = flen;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, foff, o);
+        if (lane >= o) foff += y;
+    }
+    const uint32_t total = __shfl_sync(FULL, foff, 31);
+    foff -= flen;
+    // pack the lanes' stacks in lane order (destinations never pass sources)
+    __syncwarp();
+    for (uint32_t l = 0; l < S; l++) {
+        const uint32_t so = __shfl_sync(FULL, segoff + drop, l);
+        const uint32_t dof = __shfl_sync(FULL, foff, l);
+        const uint32_t n = __shfl_sync(FULL, flen, l);
+        if (so == dof) continue;
+        for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+            const uint32_t i = b0 + lane;
+            const uint32_t v = i < n ? slot[so + i] : 0u;
+            __syncwarp();
+            if (i < n) slot[dof + i] = v;
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        r.net_ptr[out_net] = reinterpret_cast<uint64_t>(slot);
+        r.net_len[out_net] = total;
+    }
+}
+
+template <bool DEP>
+__device__ __forceinline__ void eval_segmented(const GateRec &gr, const RunDev &r, int lane) {
+    switch (gr.k) {
+    case 1: eval_gate_seg<1, DEP>(gr, r, lane); break;
+    case 2: eval_gate_seg<2, DEP>(gr, r, lane); break;
+    default: eval_gate_seg<3, DEP>(gr, r, lane); break;
+    }
+}
+
+}  // namespace seg
+
+// V = kVariantSegmented or kVariantWindowed
+template <int V, bool DEP>
+__device__ __forceinline__ void eval_variant(const GateRec &gr, const RunDev &r, unsigned char *smem_raw,
+                                             int warp, int lane) {
+    if (V == kVariantSegmented) seg::eval_segmented<DEP>(gr, r, lane);
+    else eval_windowed<DEP>(gr, r, reinterpret_cast<WarpSmem *>(smem_raw)[warp], lane);
+}
+
+template <int V>
 __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin, int32_t g_count,
                              int32_t level, RunDev r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[warp];
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(r.level_ctr + level, 1);
         g = __shfl_sync(FULL, g, 0);
         if (g >= g_count) break;
         const GateRec gr = gates[g_begin + g];
-        eval_any<false>(gr, r, sm, lane);
+        eval_variant<V, false>(gr, r, smem_raw, warp, lane);
         __syncwarp();
     }
 }
@@ -453,10 +751,10 @@ __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin,
 // Algorithm 1 without level barriers: gates are handed out in level order, so
 // every fanin gate of a handed-out gate was handed out earlier to a running
 // warp and the waits always end (the bound only guards against faults).
+template <int V>
 __global__ void dependency_kernel(const GateRec *__restrict__ gates, int32_t n_gates, int32_t ctr_slot, RunDev r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[warp];
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(r.level_ctr + ctr_slot, 1);
@@ -476,7 +774,7 @@ __global__ void dependency_kernel(const GateRec *__restrict__ gates, int32_t n_g
         }
         ok = __all_sync(FULL, ok);
         if (ok) {
-            eval_any<true>(gr, r, sm, lane);
+            eval_variant<V, true>(gr, r, smem_raw, warp, lane);
         } else if (lane == 0) {
             atomicOr(r.status, kStTimeout);
             r.net_ptr[gr.out_net] = 0;
@@ -490,24 +788,35 @@ __global__ void dependency_kernel(const GateRec *__restrict__ gates, int32_t n_g
 
 }  // namespace
 
-size_t gate_smem_bytes(int warps_per_cta) { return sizeof(WarpSmem) * (size_t)warps_per_cta; }
+size_t gate_smem_bytes(int variant, int warps_per_cta) {
+    return variant == kVariantSegmented ? 0 : sizeof(WarpSmem) * (size_t)warps_per_cta;
+}
 
-int gate_max_ctas_per_sm(int warps_per_cta) {
-    const size_t sm = gate_smem_bytes(warps_per_cta);
-    cudaFuncSetAttribute(level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(dependency_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+template <int V>
+static int max_ctas(int warps_per_cta) {
+    const size_t sm = gate_smem_bytes(V, warps_per_cta);
+    cudaFuncSetAttribute(level_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(dependency_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, level_kernel, warps_per_cta * 32, sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dependency_kernel, warps_per_cta * 32, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, level_kernel<V>, warps_per_cta * 32, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dependency_kernel<V>, warps_per_cta * 32, sm);
     return a < b ? a : b;
+}
+
+int gate_max_ctas_per_sm(int variant, int warps_per_cta) {
+    return variant == kVariantSegmented ? max_ctas<kVariantSegmented>(warps_per_cta)
+                                        : max_ctas<kVariantWindowed>(warps_per_cta);
 }
 
 cudaError_t launch_level(const GateRec *d_gates, int32_t g_begin, int32_t g_count, int32_t level,
                          const RunDev &r, const LevelCfg &cfg, cudaStream_t s) {
     if (g_count <= 0) return cudaSuccess;
     const int ctas = min(cfg.ctas, (g_count + cfg.warps_per_cta - 1) / cfg.warps_per_cta);
-    level_kernel<<<ctas, cfg.warps_per_cta * 32, gate_smem_bytes(cfg.warps_per_cta), s>>>(d_gates, g_begin,
-                                                                                          g_count, level, r);
+    const size_t sm = gate_smem_bytes(cfg.variant, cfg.warps_per_cta);
+    if (cfg.variant == kVariantSegmented)
+        level_kernel<kVariantSegmented><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
+    else
+        level_kernel<kVariantWindowed><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
     return cudaGetLastError();
 }
 
@@ -515,8 +824,11 @@ cudaError_t launch_dependency(const GateRec *d_gates, int32_t n_gates, int32_t c
                               const LevelCfg &cfg, cudaStream_t s) {
     if (n_gates <= 0) return cudaSuccess;
     const int ctas = min(cfg.ctas, (n_gates + cfg.warps_per_cta - 1) / cfg.warps_per_cta);
-    dependency_kernel<<<ctas, cfg.warps_per_cta * 32, gate_smem_bytes(cfg.warps_per_cta), s>>>(d_gates, n_gates,
-                                                                                               ctr_slot, r);
+    const size_t sm = gate_smem_bytes(cfg.variant, cfg.warps_per_cta);
+    if (cfg.variant == kVariantSegmented)
+        dependency_kernel<kVariantSegmented><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+    else
+        dependency_kernel<kVariantWindowed><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
     return cudaGetLastError();
 }
 

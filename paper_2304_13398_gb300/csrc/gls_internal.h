@@ -47,12 +47,23 @@ struct RunDev {
     int32_t n_gates;
     uint64_t wait_limit_ns;   // bound on one wait for a fanin (dependency mode)
     int32_t withhold_gate;    // test hook: this gate never publishes its flag (-1: none)
+    uint32_t seg_target;      // segmented variant: target transitions per lane segment
 };
+
+// Output slots are padded to whole 128-byte lines so that no two nets share a
+// cache line (a reader's L1 can then never hold a stale copy of a line that a
+// gate on another SM writes later in the same launch).
+constexpr uint32_t kSlotAlign = 32;   // words
+
+// Gate kernel variants: warp-wide shared-memory windows (default) or
+// per-lane time segments.
+enum { kVariantSegmented = 0, kVariantWindowed = 1 };
 
 // Launch configuration of the gate kernels.
 struct LevelCfg {
     int warps_per_cta;
     int ctas;                 // resident CTAs on the whole GPU
+    int variant;
 };
 
 // Stimulus device layout: PI i's packed transitions start at word
@@ -68,8 +79,8 @@ __host__ __device__ inline uint64_t stim_words(int64_t n_events, int64_t n_pi) {
 
 // ---- launch wrappers ----
 void set_luts(const uint64_t lut[][2], int ncells);
-size_t gate_smem_bytes(int warps_per_cta);
-int gate_max_ctas_per_sm(int warps_per_cta);
+size_t gate_smem_bytes(int variant, int warps_per_cta);
+int gate_max_ctas_per_sm(int variant, int warps_per_cta);
 // one level: gates [g_begin, g_begin + g_count) of the level-ordered array
 cudaError_t launch_level(const GateRec *d_gates, int32_t g_begin, int32_t g_count, int32_t level,
                          const RunDev &r, const LevelCfg &cfg, cudaStream_t s);

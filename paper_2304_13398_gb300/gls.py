@@ -47,7 +47,9 @@ SIGNATURES = [
     ("gls_set_option", ctypes.c_int, [P, ctypes.c_int, i64]),
     ("gls_release", ctypes.c_int, [P, i32]),
 ]
-GLS_OPT_SCHEDULE, GLS_OPT_WARPS_PER_CTA, GLS_OPT_WAIT_LIMIT_MS, GLS_OPT_TEST_WITHHOLD_GATE = 1, 2, 3, 4
+GLS_OPT_SCHEDULE, GLS_OPT_WARPS_PER_CTA, GLS_OPT_WAIT_LIMIT_MS, GLS_OPT_TEST_WITHHOLD_GATE, GLS_OPT_KERNEL, GLS_OPT_SEGMENT = 1, 2, 3, 4, 5, 6
+GLS_KERNEL_SEGMENTED, GLS_KERNEL_WINDOWED = 0, 1
+KERNELS = {"segmented": GLS_KERNEL_SEGMENTED, "windowed": GLS_KERNEL_WINDOWED}
 GLS_SCHEDULE_LEVELS, GLS_SCHEDULE_DEPENDENCY = 0, 1
 SCHEDULES = {"levels": GLS_SCHEDULE_LEVELS, "dependency": GLS_SCHEDULE_DEPENDENCY}
 
@@ -167,6 +169,10 @@ class Context:
         """'levels' (one launch per DAG level) or 'dependency' (one persistent
         launch, gates start when their fanins are done)."""
         self.set_option(GLS_OPT_SCHEDULE, SCHEDULES[name])
+
+    def set_kernel(self, name: str):
+        """'segmented' (lane per time segment) or 'windowed' (warp per window)."""
+        self.set_option(GLS_OPT_KERNEL, KERNELS[name])
 
     def load_netlist(self, nl) -> int:
         typ, fo, fn = _c(nl.type, np.uint8), _c(nl.fanin_off, np.int32), _c(nl.fanin_net, np.int32)

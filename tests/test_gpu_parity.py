@@ -13,10 +13,13 @@ pytestmark = pytest.mark.gpu
 X, Z = 2, 3
 
 
-@pytest.fixture(scope="module", params=["dependency", "levels"])
+@pytest.fixture(scope="module", params=[("segmented", "dependency"), ("segmented", "levels"),
+                                        ("windowed", "dependency"), ("windowed", "levels")],
+                ids=lambda p: f"{p[0]}-{p[1]}")
 def ctx(request):
     c = gls.Context(0)
-    c.set_schedule(request.param)
+    c.set_kernel(request.param[0])
+    c.set_schedule(request.param[1])
     yield c
     c.close()
 
