@@ -227,6 +227,48 @@ enum { GLS_SCHEDULE_LEVELS = 0, GLS_SCHEDULE_DEPENDENCY = 1 };
 /* Set a context option; GLS_EINVAL for an unknown option or value. */
 int gls_set_option(gls_ctx *ctx, int option, int64_t value);
 
+/*
+ * Simulation that allocates no device memory.  The paper has no counterpart:
+ * this entry point serves callers that cannot call cudaMalloc / cudaFree at
+ * the time they simulate -- code being captured into a CUDA graph (allocation
+ * is not a stream operation), frameworks that own all device memory through
+ * their own pool or a fixed budget, and tight loops where an allocation would
+ * synchronise the device.  The netlist and stimulus must already be loaded
+ * (loading allocates, once, at set-up); the caller passes the output store in
+ * device memory:
+ *   d_net_ptr[n_nets]    device u64: address of each net's first transition
+ *   d_net_len[n_nets]    device u32: transition count of each net
+ *   d_arena[arena_words] device u32: gate output transitions, each
+ *                        (time << 2) | value; arena_words >= 64, and the last
+ *                        64 words are kept free as read padding
+ *   d_report[4]          device u32, written at the end of the run:
+ *                        [0] status bits (1 = arena too small, 2 = carried
+ *                        transitions beyond GLS_MAX_DELAY_SPREAD, 4 = a time
+ *                        reached 2^30 - 1), [1] and [2] low and high words of
+ *                        the arena demand in words, [3] 0
+ * Nets are indexed in the netlist's device order: primary inputs first, then
+ * gates sorted by level (level_out of gls_check_netlist), equal levels in
+ * gate-id order; primary-input entries point into the loaded stimulus.  The
+ * gates run with the level schedule and the context's kernel variant.
+ * The run's scratch (per-level work counters, the arena bump pointer, the
+ * status word) lives in one statically allocated device array of
+ * GLS_NOALLOC_SCRATCH_WORDS 32-bit words (16 KiB) that every GPU which loads
+ * the library holds until the process exits; a netlist deeper than
+ * GLS_NOALLOC_MAX_LEVELS levels is rejected with GLS_ERANGE.  Each call resets
+ * that scratch, and every call on a device shares it: calls whose work
+ * overlaps on the GPU (other streams, other contexts on the same device) race
+ * and must be serialised by the caller.  The first call on each device looks
+ * up the array's device address; make that first call before any stream
+ * capture.  Stream-ordered on cuda_stream (NULL = the context's stream), no
+ * synchronisation; host-side errors (ids, sizes, GLS_ERANGE) are returned
+ * before anything is enqueued.
+ */
+#define GLS_NOALLOC_MAX_LEVELS 4000
+#define GLS_NOALLOC_SCRATCH_WORDS 4096
+int gls_simulate_noalloc(gls_ctx *ctx, int32_t netlist_id, int32_t stim_id, uint64_t *d_net_ptr,
+                         uint32_t *d_net_len, uint32_t *d_arena, int64_t arena_words, uint32_t *d_report,
+                         void *cuda_stream);
+
 /* Free a netlist, stimulus or run handle (ids are unique per context). */
 int gls_release(gls_ctx *ctx, int32_t id);
 

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <unordered_map>
@@ -406,6 +407,47 @@ int time_range_check(NetlistObj *n, StimObj *s) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Scratch of gls_simulate_noalloc: per-level work counters, the arena bump
+// pointer and the status word of a run, in one statically allocated device
+// array (words [0,1] arena top, [2] status, [64, 64 + GLS_NOALLOC_MAX_LEVELS)
+// level counters).  Every GPU that loads this library holds it until exit.
+static __device__ __align__(256) uint32_t g_noalloc_scratch[GLS_NOALLOC_SCRATCH_WORDS];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 128;
+std::mutex g_noalloc_mu;
+uint32_t *g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code cannot use the symbol itself as a device pointer).
+int noalloc_scratch(int device, uint32_t **out) {
+    if (device < 0 || device >= kNoallocMaxDevices) return fail(GLS_EINVAL, "device %d out of range", device);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(GLS_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        g_noalloc_addr[device] = static_cast<uint32_t *>(p);
+    }
+    *out = g_noalloc_addr[device];
+    return GLS_OK;
+}
+
+// Copy the run's status and arena demand from the scratch array to the
+// caller's report words.
+__global__ void noalloc_report_kernel(uint32_t *report) {
+    const unsigned long long top = *reinterpret_cast<const unsigned long long *>(g_noalloc_scratch);
+    report[0] = g_noalloc_scratch[2];
+    report[1] = (uint32_t)(top & 0xFFFFFFFFull);
+    report[2] = (uint32_t)(top >> 32);
+    report[3] = 0u;
+}
+
+}  // namespace
+
 // ===========================================================================
 extern "C" {
 
@@ -771,6 +813,56 @@ int gls_set_option(gls_ctx *c, int option, int64_t value) {
         return GLS_OK;
     }
     return fail(GLS_EINVAL, "unknown option %d", option);
+}
+
+int gls_simulate_noalloc(gls_ctx *c, int32_t netlist_id, int32_t stim_id, uint64_t *d_net_ptr,
+                         uint32_t *d_net_len, uint32_t *d_arena, int64_t arena_words, uint32_t *d_report,
+                         void *cuda_stream) {
+    if (!c) return fail(GLS_EINVAL, "NULL context");
+    if (!d_net_ptr || !d_net_len || !d_arena || !d_report) return fail(GLS_EINVAL, "NULL device buffer");
+    NetlistObj *n = find_netlist(c, netlist_id);
+    StimObj *s = find_stim(c, stim_id);
+    if (!n) return fail(GLS_EINVAL, "unknown netlist id %d", netlist_id);
+    if (!s) return fail(GLS_EINVAL, "unknown stimulus id %d", stim_id);
+    if (s->n_pi != n->n_pi) return fail(GLS_EINVAL, "stimulus has %d PIs, netlist %d", s->n_pi, n->n_pi);
+    if (n->lv.depth > GLS_NOALLOC_MAX_LEVELS)
+        return fail(GLS_ERANGE, "netlist depth %d exceeds the %d levels of the no-allocation scratch",
+                    n->lv.depth, GLS_NOALLOC_MAX_LEVELS);
+    if (arena_words < 2 * (int64_t)kSlotAlign)
+        return fail(GLS_EINVAL, "arena of %lld words is below the %u-word minimum", (long long)arena_words,
+                    2 * kSlotAlign);
+    int rc = time_range_check(n, s);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    uint32_t *scratch = nullptr;
+    rc = noalloc_scratch(c->device, &scratch);
+    if (rc) return rc;
+    RunDev r{};
+    r.net_ptr = d_net_ptr;
+    r.net_len = d_net_len;
+    r.arena = d_arena;
+    r.arena_cap = (uint64_t)arena_words - 2 * kSlotAlign;   // the last words stay as read padding
+    r.arena_top = reinterpret_cast<unsigned long long *>(scratch);
+    r.status = scratch + 2;
+    r.level_ctr = reinterpret_cast<int32_t *>(scratch + 64);
+    r.done = nullptr;
+    r.n_pi = n->n_pi;
+    r.n_gates = n->n_gates;
+    r.wait_limit_ns = c->wait_limit_ns;
+    r.withhold_gate = -1;
+    r.seg_target = c->seg_target;
+    cudaStream_t st = pick_stream(c, cuda_stream);
+    // run_init zeroes the counters (one per level, all inside the array because
+    // depth <= GLS_NOALLOC_MAX_LEVELS), the arena top and the status left by
+    // the previous call
+    CK(launch_run_init(s->d_off, s->d_packed, r, n->lv.depth, st));
+    for (int32_t L = 1; L <= n->lv.depth; L++) {
+        const int32_t b = n->lv.level_begin[L], cnt = n->lv.level_begin[L + 1] - b;
+        CK(launch_level(n->d_gates, b, cnt, L - 1, r, c->cfg, st));
+    }
+    noalloc_report_kernel<<<1, 1, 0, st>>>(d_report);
+    CK(cudaGetLastError());
+    return GLS_OK;
 }
 
 int gls_release(gls_ctx *c, int32_t id) {

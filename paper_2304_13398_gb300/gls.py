@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "GLS_OK", -1: "GLS_EINVAL", -2: "GLS_ECYCLE", -3: "GLS_ESTIM"
                 -5: "GLS_ENOMEM", -6: "GLS_EOVERFLOW", -7: "GLS_ETIMEOUT", -8: "GLS_ECUDA"}
 CELLS = ["INV", "BUF", "AND2", "OR2", "NAND2", "NOR2", "XOR2", "XNOR2", "MUX2", "AOI21", "OAI21"]
 GLS_MAX_DELAY_SPREAD = 255
+GLS_NOALLOC_MAX_LEVELS = 4000
 
 P = ctypes.c_void_p
 i32, i64, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
@@ -45,6 +46,7 @@ SIGNATURES = [
     ("gls_read_waveform", ctypes.c_int, [P, i32, i32, P, P, i64, ctypes.POINTER(i64)]),
     ("gls_read_all", ctypes.c_int, [P, i32, P, P, i64]),
     ("gls_set_option", ctypes.c_int, [P, ctypes.c_int, i64]),
+    ("gls_simulate_noalloc", ctypes.c_int, [P, i32, i32, P, P, P, i64, P, P]),
     ("gls_release", ctypes.c_int, [P, i32]),
 ]
 GLS_OPT_SCHEDULE, GLS_OPT_WARPS_PER_CTA, GLS_OPT_WAIT_LIMIT_MS, GLS_OPT_TEST_WITHHOLD_GATE, GLS_OPT_KERNEL, GLS_OPT_SEGMENT = 1, 2, 3, 4, 5, 6
