@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--arena-words", type=int, default=0, help="event arena size (0: size from a first run)")
     ap.add_argument("--schedule", default="dependency", choices=["dependency", "levels"])
     ap.add_argument("--warps-per-cta", type=int, default=0)
-    ap.add_argument("--kernel", default="windowed", choices=["windowed", "segmented"])
+    ap.add_argument("--kernel", default="windowed", choices=["windowed", "wide", "segmented"])
     ap.add_argument("--segment", type=int, default=0, help="segmented kernel: transitions per lane segment")
     return ap.parse_args()
 

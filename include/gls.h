@@ -208,12 +208,13 @@ typedef enum gls_option {
                                    (default 32); a gate uses min(32, ceil(inputs / this)) lanes */
 } gls_option;
 
-/* Gate kernel variants; both compute the same waveforms.
+/* Gate kernel variants; all compute the same waveforms.
    SEGMENTED: each lane of a warp evaluates one time segment of the gate
    sequentially and the segments are reconciled once per gate.
-   WINDOWED: the warp streams shared-memory windows of all pins and merges,
-   evaluates and filters each window cooperatively. */
-enum { GLS_KERNEL_SEGMENTED = 0, GLS_KERNEL_WINDOWED = 1 };
+   WINDOWED / WINDOWED_WIDE: the warp streams shared-memory windows of 128 /
+   256 transitions per pin and merges, evaluates and filters each window
+   cooperatively. */
+enum { GLS_KERNEL_SEGMENTED = 0, GLS_KERNEL_WINDOWED = 1, GLS_KERNEL_WINDOWED_WIDE = 2 };
 
 /* Schedules of the gate evaluation (Sec. 4.1).
    LEVELS: one kernel launch per DAG level (the topological-layer partition

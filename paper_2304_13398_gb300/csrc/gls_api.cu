@@ -799,9 +799,10 @@ int gls_set_option(gls_ctx *c, int option, int64_t value) {
         c->wait_limit_ns = (uint64_t)value * 1000000ull;
         return GLS_OK;
     case GLS_OPT_KERNEL:
-        if (value != GLS_KERNEL_SEGMENTED && value != GLS_KERNEL_WINDOWED)
+        if (value != GLS_KERNEL_SEGMENTED && value != GLS_KERNEL_WINDOWED && value != GLS_KERNEL_WINDOWED_WIDE)
             return fail(GLS_EINVAL, "unknown kernel variant %lld", (long long)value);
-        return apply_launch_cfg(c, value == GLS_KERNEL_SEGMENTED ? kVariantSegmented : kVariantWindowed,
+        return apply_launch_cfg(c, value == GLS_KERNEL_SEGMENTED ? kVariantSegmented
+                                   : value == GLS_KERNEL_WINDOWED ? kVariantWindowed : kVariantWindowedWide,
                                 c->cfg.warps_per_cta);
     case GLS_OPT_SEGMENT:
         if (value < 1 || value > (1 << 20)) return fail(GLS_EINVAL, "segment target must be in [1, 2^20]");

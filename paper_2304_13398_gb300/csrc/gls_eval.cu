@@ -50,19 +50,27 @@ void set_luts(const uint64_t lut[][2], int ncells) {
 
 namespace {
 
-constexpr int CH = 128;                 // transitions per pin window
-constexpr int WIN = CH + 8;             // aligned lead (<= 3) + CH + sentinel, multiple of 4
 constexpr int PCAP = 256;               // carried (pending) transitions, > GLS_MAX_DELAY_SPREAD
-constexpr int QCAP = PCAP + 3 * CH;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr uint32_t EINF = 0xFFFFFFFFu;  // sentinel event; its time 2^30-1 exceeds every real time
 
+// Shared memory of one warp of the windowed variant with CH transitions per
+// pin window.
+template <int CH>
 struct __align__(16) WarpSmem {
+    static constexpr int WIN = CH + 8;     // aligned lead (<= 3) + CH + sentinel, multiple of 4
     uint32_t win[2][3][WIN];  // double-buffered pin windows
     uint32_t B[2 * CH + 4];   // pins a+b merged (3-input cells), sentinel-terminated
     uint16_t Binfo[2 * CH];   // source of B[i]: pin b flag (bit 15) | index in its window
     uint32_t cand[3 * CH];    // per-lane stacks of scheduled transitions (t_r << 2 | v)
-    uint32_t Q[QCAP];         // carried + surviving transitions of the chunk
+    uint32_t Q[PCAP + 3 * CH];  // carried transitions (front) + this chunk's survivors
+};
+
+// Running state of one gate's output between chunks.
+struct CommitState {
+    uint32_t outCount;   // transitions written
+    uint32_t lastV;      // value of the last final survivor (kept or dropped)
+    int np;              // carried transitions in Q[0..np)
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -117,9 +125,9 @@ __device__ __forceinline__ uint32_t pin_delay(const GateCtx &g, int p, uint32_t 
 // Issue the asynchronous copies of every pin's next window into buffer b.
 // Window p covers transitions [cur[p], cur[p] + n[p]); the copy starts at the
 // 16-byte boundary below cur[p] (lead[p] <= 3 words) and ends at a multiple
-// of 4 words, which stays inside the net's slot (slots are padded to 4 words).
-template <int K>
-__device__ __forceinline__ bool issue_windows(WarpSmem &sm, int b, const GateCtx &g, const uint32_t *cur,
+// of 4 words, which stays inside the net's slot (slots are padded).
+template <int K, int CH>
+__device__ __forceinline__ bool issue_windows(WarpSmem<CH> &sm, int b, const GateCtx &g, const uint32_t *cur,
                                               int *lead, int *n, int lane) {
     bool any = false;
 #pragma unroll
@@ -139,8 +147,77 @@ __device__ __forceinline__ bool issue_windows(WarpSmem &sm, int b, const GateCtx
     return any;
 }
 
-template <int K, bool DEP>
-__device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem &sm, int lane) {
+// Steps 4 and 5 of a chunk, shared by every pin count.  Lane l's stack is
+// cand[d0, top).  Returns false when more than PCAP transitions would be
+// carried.
+template <int CH>
+__device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0, int top, uint32_t Tfin, uint32_t *out,
+                                          CommitState &cs) {
+    const uint32_t lanemask_lt = (1u << lane) - 1u;
+    // Eq. 1 across lanes (suffix minimum of the later lanes' smallest t_r)
+    // and against the carried transitions (minimum over the whole chunk)
+    const uint32_t mn = top > d0 ? (sm.cand[d0] >> 2) : kTimeInf;
+    uint32_t inc = mn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_down_sync(FULL, inc, o);
+        if (lane + o < 32) inc = min(inc, y);
+    }
+    uint32_t after = __shfl_down_sync(FULL, inc, 1);
+    if (lane == 31) after = kTimeInf;
+    const uint32_t Mall = __shfl_sync(FULL, inc, 0);
+    while (top > d0 && (sm.cand[top - 1] >> 2) >= after) top--;
+    const int np = cs.np;
+    int npk = 0;
+    for (int b0 = 0; b0 < np; b0 += 32) {
+        const int idx = b0 + lane;
+        npk += __popc(__ballot_sync(FULL, idx < np && (sm.Q[idx] >> 2) < Mall));
+    }
+    // survivors, in order, behind the carried ones that survive
+    const uint32_t cnt = (uint32_t)(top - d0);
+    uint32_t pre = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, pre, o);
+        if (lane >= o) pre += y;
+    }
+    const int total = (int)__shfl_sync(FULL, pre, 31);
+    const int pos = npk + (int)(pre - cnt);
+    __syncwarp();
+    for (uint32_t x = 0; x < cnt; x++) sm.Q[pos + x] = sm.cand[d0 + x];
+    const int nQ = npk + total;
+    __syncwarp();
+    // commit the final prefix (t_r < Tfin), dropping repeats (Fig. 6)
+    int nf = 0;
+    uint32_t outCount = cs.outCount;
+    for (int b0 = 0; b0 < nQ; b0 += 32) {
+        const int idx = b0 + lane;
+        const uint32_t e = idx < nQ ? sm.Q[idx] : 0u;
+        const bool fin = idx < nQ && (e >> 2) < Tfin;
+        const uint32_t pv = idx == 0 ? cs.lastV : (idx < nQ ? (sm.Q[idx - 1] & 3u) : 0u);
+        const bool keep = fin && ((e & 3u) != pv);
+        const uint32_t bk = __ballot_sync(FULL, keep);
+        if (keep) out[outCount + __popc(bk & lanemask_lt)] = e;
+        outCount += __popc(bk);
+        nf += __popc(__ballot_sync(FULL, fin));
+    }
+    cs.outCount = outCount;
+    if (nf > 0) cs.lastV = sm.Q[nf - 1] & 3u;
+    // carry the rest to the front of Q
+    const int npn = nQ - nf;
+    if (npn > PCAP) return false;
+    for (int b0 = 0; b0 < npn; b0 += 32) {
+        const int idx = b0 + lane;
+        const uint32_t e = idx < npn ? sm.Q[nf + idx] : 0u;
+        __syncwarp();
+        if (idx < npn) sm.Q[idx] = e;
+    }
+    cs.np = npn;
+    return true;
+}
+
+template <int K, bool DEP, int CH>
+__device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane) {
     GateCtx g;
     uint64_t bound = 0;
 #pragma unroll
@@ -196,15 +273,12 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem &sm, int 
     const uint32_t lut2 = (uint32_t)g.lut_hi;
 
     uint32_t carry = 0x2Au;           // pins a, b, c at X before the first transition
-    uint32_t lastV = kVX;             // value of the last committed survivor
-    uint32_t outCount = 0;
-    int np = 0;                       // carried transitions in Q[0..np)
+    CommitState cs{0u, kVX, 0};
     uint32_t cur[3] = {0, 0, 0};
-    const uint32_t lanemask_lt = (1u << lane) - 1u;
     bool failed = false;
     int b = 0;
     int lead[3] = {0, 0, 0}, n[3] = {0, 0, 0};
-    bool more = issue_windows<K>(sm, 0, g, cur, lead, n, lane);
+    bool more = issue_windows<K, CH>(sm, 0, g, cur, lead, n, lane);
 
     while (more) {
         cp_async_wait_all();
@@ -235,7 +309,7 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem &sm, int 
 #pragma unroll
         for (int p = 0; p < K; p++) ncur[p] += (uint32_t)m[p];
         int nlead[3] = {0, 0, 0}, nn[3] = {0, 0, 0};
-        more = issue_windows<K>(sm, b ^ 1, g, ncur, nlead, nn, lane);
+        more = issue_windows<K, CH>(sm, b ^ 1, g, ncur, nlead, nn, lane);
         if (lane < K) {   // sentinels after the consumed part of every window
             const int at = lane == 0 ? lead[0] + m[0] : (lane == 1 ? lead[1] + m[1] : lead[2] + m[2]);
             sm.win[b][lane][at] = EINF;
@@ -354,61 +428,9 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem &sm, int 
         }
         if (trmax >= kTimeLimit) atomicOr(r.status, kStTimeRange);
 
-        // ---- 4. Eq. 1 across lanes and against the carried transitions ----
-        const uint32_t mn = top > d0 ? (sm.cand[d0] >> 2) : kTimeInf;
-        uint32_t inc = mn;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_down_sync(FULL, inc, o);
-            if (lane + o < 32) inc = min(inc, y);
-        }
-        uint32_t after = __shfl_down_sync(FULL, inc, 1);
-        if (lane == 31) after = kTimeInf;
-        const uint32_t Mall = __shfl_sync(FULL, inc, 0);
-        while (top > d0 && (sm.cand[top - 1] >> 2) >= after) top--;
-        int npk = 0;
-        for (int b0 = 0; b0 < np; b0 += 32) {
-            const int idx = b0 + lane;
-            npk += __popc(__ballot_sync(FULL, idx < np && (sm.Q[idx] >> 2) < Mall));
-        }
-        const uint32_t cnt = (uint32_t)(top - d0);
-        uint32_t pre = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, pre, o);
-            if (lane >= o) pre += y;
-        }
-        const int total = (int)__shfl_sync(FULL, pre, 31);
-        const int pos = npk + (int)(pre - cnt);
-        __syncwarp();
-        for (uint32_t x = 0; x < cnt; x++) sm.Q[pos + x] = sm.cand[d0 + x];
-        const int nQ = npk + total;
-        __syncwarp();
-
-        // ---- 5. commit what no later transition can deny; drop repeats ----
+        // ---- 4./5. Eq. 1 across lanes, commit, carry ----
         const uint32_t Tfin = last ? kTimeInf : Tend + 1u + g.dmin;
-        int nf = 0;
-        for (int b0 = 0; b0 < nQ; b0 += 32) {
-            const int idx = b0 + lane;
-            const uint32_t e = idx < nQ ? sm.Q[idx] : 0u;
-            const bool fin = idx < nQ && (e >> 2) < Tfin;
-            const uint32_t pv = idx == 0 ? lastV : (idx < nQ ? (sm.Q[idx - 1] & 3u) : 0u);
-            const bool keep = fin && ((e & 3u) != pv);
-            const uint32_t bk = __ballot_sync(FULL, keep);
-            if (keep) out[outCount + __popc(bk & lanemask_lt)] = e;
-            outCount += __popc(bk);
-            nf += __popc(__ballot_sync(FULL, fin));
-        }
-        if (nf > 0) lastV = sm.Q[nf - 1] & 3u;
-        const int npn = nQ - nf;
-        if (npn > PCAP) { failed = true; break; }
-        for (int b0 = 0; b0 < npn; b0 += 32) {
-            const int idx = b0 + lane;
-            const uint32_t e = idx < npn ? sm.Q[nf + idx] : 0u;
-            __syncwarp();
-            if (idx < npn) sm.Q[idx] = e;
-        }
-        np = npn;
+        if (!commit_chunk<CH>(sm, lane, d0, top, Tfin, out, cs)) { failed = true; break; }
 #pragma unroll
         for (int p = 0; p < K; p++)
             if (m[p] > 0) carry = setpin(carry, p, A[p][m[p] - 1] & 3u);
@@ -421,16 +443,16 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem &sm, int 
     if (lane == 0) {
         if (failed) atomicOr(r.status, kStPendingOverflow);
         r.net_ptr[out_net] = reinterpret_cast<uint64_t>(out);
-        r.net_len[out_net] = failed ? 0u : outCount;
+        r.net_len[out_net] = failed ? 0u : cs.outCount;
     }
 }
 
-template <bool DEP>
-__device__ __forceinline__ void eval_windowed(const GateRec &gr, const RunDev &r, WarpSmem &sm, int lane) {
+template <bool DEP, int CH>
+__device__ __forceinline__ void eval_windowed(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane) {
     switch (gr.k) {
-    case 1: eval_gate<1, DEP>(gr, r, sm, lane); break;
-    case 2: eval_gate<2, DEP>(gr, r, sm, lane); break;
-    default: eval_gate<3, DEP>(gr, r, sm, lane); break;
+    case 1: eval_gate<1, DEP, CH>(gr, r, sm, lane); break;
+    case 2: eval_gate<2, DEP, CH>(gr, r, sm, lane); break;
+    default: eval_gate<3, DEP, CH>(gr, r, sm, lane); break;
     }
 }
 
@@ -729,7 +751,8 @@ template <int V, bool DEP>
 __device__ __forceinline__ void eval_variant(const GateRec &gr, const RunDev &r, unsigned char *smem_raw,
                                              int warp, int lane) {
     if (V == kVariantSegmented) seg::eval_segmented<DEP>(gr, r, lane);
-    else eval_windowed<DEP>(gr, r, reinterpret_cast<WarpSmem *>(smem_raw)[warp], lane);
+    else if (V == kVariantWindowedWide) eval_windowed<DEP, 256>(gr, r, reinterpret_cast<WarpSmem<256> *>(smem_raw)[warp], lane);
+    else eval_windowed<DEP, 128>(gr, r, reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane);
 }
 
 template <int V>
@@ -789,7 +812,8 @@ __global__ void dependency_kernel(const GateRec *__restrict__ gates, int32_t n_g
 }  // namespace
 
 size_t gate_smem_bytes(int variant, int warps_per_cta) {
-    return variant == kVariantSegmented ? 0 : sizeof(WarpSmem) * (size_t)warps_per_cta;
+    if (variant == kVariantSegmented) return 0;
+    return (variant == kVariantWindowedWide ? sizeof(WarpSmem<256>) : sizeof(WarpSmem<128>)) * (size_t)warps_per_cta;
 }
 
 template <int V>
@@ -804,8 +828,9 @@ static int max_ctas(int warps_per_cta) {
 }
 
 int gate_max_ctas_per_sm(int variant, int warps_per_cta) {
-    return variant == kVariantSegmented ? max_ctas<kVariantSegmented>(warps_per_cta)
-                                        : max_ctas<kVariantWindowed>(warps_per_cta);
+    if (variant == kVariantSegmented) return max_ctas<kVariantSegmented>(warps_per_cta);
+    if (variant == kVariantWindowedWide) return max_ctas<kVariantWindowedWide>(warps_per_cta);
+    return max_ctas<kVariantWindowed>(warps_per_cta);
 }
 
 cudaError_t launch_level(const GateRec *d_gates, int32_t g_begin, int32_t g_count, int32_t level,
@@ -815,6 +840,8 @@ cudaError_t launch_level(const GateRec *d_gates, int32_t g_begin, int32_t g_coun
     const size_t sm = gate_smem_bytes(cfg.variant, cfg.warps_per_cta);
     if (cfg.variant == kVariantSegmented)
         level_kernel<kVariantSegmented><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
+    else if (cfg.variant == kVariantWindowedWide)
+        level_kernel<kVariantWindowedWide><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
     else
         level_kernel<kVariantWindowed><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
     return cudaGetLastError();
@@ -827,6 +854,8 @@ cudaError_t launch_dependency(const GateRec *d_gates, int32_t n_gates, int32_t c
     const size_t sm = gate_smem_bytes(cfg.variant, cfg.warps_per_cta);
     if (cfg.variant == kVariantSegmented)
         dependency_kernel<kVariantSegmented><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+    else if (cfg.variant == kVariantWindowedWide)
+        dependency_kernel<kVariantWindowedWide><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
     else
         dependency_kernel<kVariantWindowed><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
     return cudaGetLastError();

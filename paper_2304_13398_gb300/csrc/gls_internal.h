@@ -55,9 +55,9 @@ struct RunDev {
 // gate on another SM writes later in the same launch).
 constexpr uint32_t kSlotAlign = 32;   // words
 
-// Gate kernel variants: warp-wide shared-memory windows (default) or
-// per-lane time segments.
-enum { kVariantSegmented = 0, kVariantWindowed = 1 };
+// Gate kernel variants: warp-wide shared-memory windows of 128 (default) or
+// 256 transitions per pin, or per-lane time segments.
+enum { kVariantSegmented = 0, kVariantWindowed = 1, kVariantWindowedWide = 2 };
 
 // Launch configuration of the gate kernels.
 struct LevelCfg {

@@ -50,8 +50,8 @@ SIGNATURES = [
     ("gls_release", ctypes.c_int, [P, i32]),
 ]
 GLS_OPT_SCHEDULE, GLS_OPT_WARPS_PER_CTA, GLS_OPT_WAIT_LIMIT_MS, GLS_OPT_TEST_WITHHOLD_GATE, GLS_OPT_KERNEL, GLS_OPT_SEGMENT = 1, 2, 3, 4, 5, 6
-GLS_KERNEL_SEGMENTED, GLS_KERNEL_WINDOWED = 0, 1
-KERNELS = {"segmented": GLS_KERNEL_SEGMENTED, "windowed": GLS_KERNEL_WINDOWED}
+GLS_KERNEL_SEGMENTED, GLS_KERNEL_WINDOWED, GLS_KERNEL_WINDOWED_WIDE = 0, 1, 2
+KERNELS = {"segmented": GLS_KERNEL_SEGMENTED, "windowed": GLS_KERNEL_WINDOWED, "wide": GLS_KERNEL_WINDOWED_WIDE}
 GLS_SCHEDULE_LEVELS, GLS_SCHEDULE_DEPENDENCY = 0, 1
 SCHEDULES = {"levels": GLS_SCHEDULE_LEVELS, "dependency": GLS_SCHEDULE_DEPENDENCY}
 
@@ -173,7 +173,8 @@ class Context:
         self.set_option(GLS_OPT_SCHEDULE, SCHEDULES[name])
 
     def set_kernel(self, name: str):
-        """'segmented' (lane per time segment) or 'windowed' (warp per window)."""
+        """'windowed' (warp per 128-transition window), 'wide' (256) or
+        'segmented' (lane per time segment)."""
         self.set_option(GLS_OPT_KERNEL, KERNELS[name])
 
     def load_netlist(self, nl) -> int:

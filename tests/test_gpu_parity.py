@@ -13,8 +13,9 @@ pytestmark = pytest.mark.gpu
 X, Z = 2, 3
 
 
-@pytest.fixture(scope="module", params=[("segmented", "dependency"), ("segmented", "levels"),
-                                        ("windowed", "dependency"), ("windowed", "levels")],
+@pytest.fixture(scope="module", params=[("windowed", "dependency"), ("windowed", "levels"),
+                                        ("wide", "dependency"), ("wide", "levels"),
+                                        ("segmented", "dependency"), ("segmented", "levels")],
                 ids=lambda p: f"{p[0]}-{p[1]}")
 def ctx(request):
     c = gls.Context(0)
