@@ -169,7 +169,7 @@ def kernel_source_sha():
 def ncu_traffic(workload: str):
     """DRAM bytes per run of the level kernel from a committed ncu summary,
     valid only while the kernel source is unchanged."""
-    p = os.path.join(ROOT, "profiles", "level_kernel_traffic.json")
+    p = os.path.join(ROOT, "profiles", "gate_kernel_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
@@ -348,7 +348,9 @@ def run_own(a):
     achieved = alg_bytes / (k_ms / 1000.0) / 1e9
     traffic = ncu_traffic(a.workload)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_kind": peak_kind, "kernel": "level_kernel (all levels of one run)",
+            "traffic": traffic, "peak_kind": peak_kind,
+            "kernel": (f"dependency_kernel<{a.kernel}> (one launch per run)" if a.schedule == "dependency"
+                       else f"level_kernel<{a.kernel}> (all levels of one run)"),
             "algorithmic_bytes_per_run": alg_bytes, "kernel_ms_per_run": k_ms}
     cb = None
     if rank == 0 and world == 1 and not a.no_cpu:

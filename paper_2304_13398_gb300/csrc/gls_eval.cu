@@ -821,6 +821,10 @@ static int max_ctas(int warps_per_cta) {
     const size_t sm = gate_smem_bytes(V, warps_per_cta);
     cudaFuncSetAttribute(level_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(dependency_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 0) {   // the windowed variants are limited by shared memory: prefer the largest carveout
+        cudaFuncSetAttribute(level_kernel<V>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(dependency_kernel<V>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
     int a = 0, b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, level_kernel<V>, warps_per_cta * 32, sm);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dependency_kernel<V>, warps_per_cta * 32, sm);
