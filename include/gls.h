@@ -162,6 +162,22 @@ int gls_update_stimulus(gls_ctx *ctx, int32_t stim_id, const int64_t *off, const
 int gls_simulate(gls_ctx *ctx, int32_t netlist_id, int32_t stim_id, int64_t arena_events,
                  void *cuda_stream, int32_t *run_id);
 
+/*
+ * Batched simulation: n_items (netlist, stimulus) pairs -- the same netlist
+ * with many stimulus sets, distinct netlists, or both -- evaluated by one
+ * graph launch as one disjoint union: their gates are interleaved by level
+ * into one work order, so the dependency schedule's single persistent launch
+ * (or one launch per level) covers every item and the long gates of one item
+ * overlap with the work of the others.  netlist_ids[n_items] and
+ * stim_ids[n_items] are loaded handles; arena_events as in gls_simulate
+ * (0 = 256 words per stimulus transition of all items plus 2^20, capped at
+ * half the unused budget).  Read items back with gls_read_item; gls_run_stats
+ * reports all items together.  No counterpart in the paper (Sec. 4 simulates
+ * one netlist at a time); each item's waveforms equal a gls_simulate of it.
+ */
+int gls_simulate_batch(gls_ctx *ctx, int32_t n_items, const int32_t *netlist_ids, const int32_t *stim_ids,
+                       int64_t arena_events, void *cuda_stream, int32_t *run_id);
+
 /* Enqueue the same run again (same buffers, current stimulus contents). */
 int gls_rerun(gls_ctx *ctx, int32_t run_id, void *cuda_stream);
 
@@ -179,8 +195,8 @@ int gls_rerun(gls_ctx *ctx, int32_t run_id, void *cuda_stream);
 int gls_run_stats(gls_ctx *ctx, int32_t run_id, int64_t *total_events, double *kernel_ms);
 
 /*
- * Copy one net's waveform to the host: times into t[cap], values into
- * v[cap].  *n_out always receives the length; GLS_EOVERFLOW if cap < length
+ * Copy one net's waveform to the host (item 0 of a batch): times into
+ * t[cap], values into v[cap].  *n_out always receives the length; GLS_EOVERFLOW if cap < length
  * (nothing copied).  Synchronises with the run.
  */
 int gls_read_waveform(gls_ctx *ctx, int32_t run_id, int32_t net, int32_t *t, uint8_t *v,
@@ -269,6 +285,13 @@ int gls_set_option(gls_ctx *ctx, int option, int64_t value);
 int gls_simulate_noalloc(gls_ctx *ctx, int32_t netlist_id, int32_t stim_id, uint64_t *d_net_ptr,
                          uint32_t *d_net_len, uint32_t *d_arena, int64_t arena_words, uint32_t *d_report,
                          void *cuda_stream);
+
+/*
+ * gls_read_all for item 'item' of a run (0 for runs made by gls_simulate,
+ * whose read calls refer to their only item): off[n_nets(item) + 1] and
+ * packed[cap] as in gls_read_all, nets in the item's caller order.
+ */
+int gls_read_item(gls_ctx *ctx, int32_t run_id, int32_t item, int64_t *off, uint32_t *packed, int64_t cap);
 
 /* Free a netlist, stimulus or run handle (ids are unique per context). */
 int gls_release(gls_ctx *ctx, int32_t id);

@@ -214,6 +214,7 @@ struct NetlistObj {
     GateRec *d_gates = nullptr;
     int32_t *d_ext2int = nullptr;      // [N] caller net id -> internal net id
     std::vector<int32_t> ext2int;      // host copy
+    std::vector<GateRec> recs;         // host copy of the level-ordered records (batches)
 };
 
 struct StimObj {
@@ -226,18 +227,31 @@ struct StimObj {
     uint32_t *d_packed = nullptr;
 };
 
-struct RunObj {
+// One (netlist, stimulus) instance of a run; its nets occupy the combined
+// net ids [net_base, net_base + n_pi + n_gates) in internal order.
+struct RunItem {
     int32_t netlist_id = 0, stim_id = 0;
+    int64_t net_base = 0;
+};
+
+struct RunObj {
+    std::vector<RunItem> items;
+    int64_t n_nets = 0;                 // all instances
+    int32_t n_gates = 0;
+    int32_t depth = 0;                  // deepest instance
+    std::vector<int32_t> level_begin;   // gates of level L at [level_begin[L], level_begin[L+1])
+    GateRec *d_gates = nullptr;         // level-ordered records of all instances
+    bool owns_gates = false;            // batches own a combined copy
     RunDev dev{};
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     unsigned long long *d_sum = nullptr;
-    int64_t *d_off = nullptr;          // [N+1] for read_all
+    int64_t *d_off = nullptr;          // [max nets + 1] for read-back
+    int64_t off_cap = 0;
     int64_t *d_scan_tmp = nullptr;
     size_t scan_tmp = 0;
     uint32_t *d_gather = nullptr;
     int64_t gather_cap = 0;
-    bool launched = false;
     int schedule = 0;
 };
 
@@ -312,6 +326,7 @@ void free_run(gls_ctx *c, RunObj *r) {
     if (r->exec) cudaGraphExecDestroy(r->exec);
     if (r->ev0) cudaEventDestroy(r->ev0);
     if (r->ev1) cudaEventDestroy(r->ev1);
+    if (r->owns_gates) dfree(c, r->d_gates);
     dfree(c, r->dev.net_ptr);
     dfree(c, r->dev.net_len);
     dfree(c, r->dev.arena);
@@ -363,21 +378,33 @@ RunObj *find_run(gls_ctx *c, int32_t id) {
     return it == c->runs.end() ? nullptr : it->second.get();
 }
 
-int build_run_graph(gls_ctx *c, RunObj *r, NetlistObj *n, StimObj *s) {
+int build_run_graph(gls_ctx *c, RunObj *r) {
     cudaGraph_t graph = nullptr;
-    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = launch_run_init(s->d_off, s->d_packed, r->dev, n->lv.depth + 1, c->cap_stream);
-    if (e == cudaSuccess) e = cudaEventRecordWithFlags(r->ev0, c->cap_stream, cudaEventRecordExternal);
-    if (r->schedule == GLS_SCHEDULE_DEPENDENCY) {
-        if (e == cudaSuccess) e = launch_dependency(n->d_gates, n->n_gates, n->lv.depth, r->dev, c->cfg, c->cap_stream);
+    const bool dep = r->schedule == GLS_SCHEDULE_DEPENDENCY;
+    cudaStream_t cs = c->cap_stream;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(r->dev.level_ctr, 0, sizeof(int32_t) * ((size_t)r->depth + 1), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->dev.arena_top, 0, sizeof(unsigned long long), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->dev.status, 0, sizeof(uint32_t), cs);
+    if (e == cudaSuccess && dep) e = cudaMemsetAsync(r->dev.done, 0, sizeof(uint32_t) * (size_t)r->n_nets, cs);
+    for (const RunItem &it : r->items) {
+        if (e != cudaSuccess) break;
+        NetlistObj *n = find_netlist(c, it.netlist_id);
+        StimObj *s = find_stim(c, it.stim_id);
+        e = launch_pi_init(s->d_off, s->d_packed, n->n_pi, it.net_base, r->dev.net_ptr, r->dev.net_len,
+                           dep ? r->dev.done : nullptr, cs);
+    }
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(r->ev0, cs, cudaEventRecordExternal);
+    if (dep) {
+        if (e == cudaSuccess) e = launch_dependency(r->d_gates, r->n_gates, r->depth, r->dev, c->cfg, cs);
     } else {
-        for (int32_t L = 1; L <= n->lv.depth && e == cudaSuccess; L++) {
-            int32_t b = n->lv.level_begin[L], cnt = n->lv.level_begin[L + 1] - b;
-            e = launch_level(n->d_gates, b, cnt, L - 1, r->dev, c->cfg, c->cap_stream);
+        for (int32_t L = 1; L <= r->depth && e == cudaSuccess; L++) {
+            const int32_t b = r->level_begin[L], cnt = r->level_begin[L + 1] - b;
+            e = launch_level(r->d_gates, b, cnt, L - 1, r->dev, c->cfg, cs);
         }
     }
-    if (e == cudaSuccess) e = cudaEventRecordWithFlags(r->ev1, c->cap_stream, cudaEventRecordExternal);
-    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(r->ev1, cs, cudaEventRecordExternal);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         return fail(GLS_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
@@ -402,6 +429,144 @@ int time_range_check(NetlistObj *n, StimObj *s) {
     if ((int64_t)s->max_time + n->lv.max_path_delay >= (int64_t)kTimeLimit)
         return fail(GLS_ERANGE, "latest input time %u + longest path delay %lld reaches 2^30-1", s->max_time,
                     (long long)n->lv.max_path_delay);
+    return GLS_OK;
+}
+
+int items_time_range_check(gls_ctx *c, const RunObj *r) {
+    for (const RunItem &it : r->items) {
+        int rc = time_range_check(find_netlist(c, it.netlist_id), find_stim(c, it.stim_id));
+        if (rc) return rc;
+    }
+    return GLS_OK;
+}
+
+// Validate the instances, lay out their nets and gates, allocate the store and
+// capture the run's graph; the run is launched by the caller.
+int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, int32_t n_items,
+               int64_t arena_events, std::unique_ptr<RunObj> &out) {
+    auto r = std::make_unique<RunObj>();
+    r->schedule = c->schedule;
+    int64_t stim_events = 0, base = 0;
+    for (int32_t i = 0; i < n_items; i++) {
+        NetlistObj *n = find_netlist(c, netlist_ids[i]);
+        StimObj *s = find_stim(c, stim_ids[i]);
+        if (!n) return fail(GLS_EINVAL, "item %d: unknown netlist id %d", i, netlist_ids[i]);
+        if (!s) return fail(GLS_EINVAL, "item %d: unknown stimulus id %d", i, stim_ids[i]);
+        if (s->n_pi != n->n_pi) return fail(GLS_EINVAL, "item %d: stimulus has %d PIs, netlist %d", i, s->n_pi, n->n_pi);
+        int rc = time_range_check(n, s);
+        if (rc) return rc;
+        r->items.push_back(RunItem{netlist_ids[i], stim_ids[i], base});
+        base += (int64_t)n->n_pi + n->n_gates;
+        r->n_gates += n->n_gates;
+        r->depth = std::max(r->depth, n->lv.depth);
+        stim_events += s->n_events;
+    }
+    if (base >= (int64_t)INT32_MAX) return fail(GLS_EINVAL, "a run holds at most 2^31 - 1 nets");
+    r->n_nets = base;
+    int rc = GLS_OK;
+    if (n_items == 1) {   // one instance: its own records and levels
+        NetlistObj *n = find_netlist(c, netlist_ids[0]);
+        r->d_gates = n->d_gates;
+        r->level_begin = n->lv.level_begin;
+    } else {              // records of all instances interleaved by level, net ids shifted
+        std::vector<GateRec> comb((size_t)std::max(r->n_gates, 1));
+        r->level_begin.assign(r->depth + 2, 0);
+        size_t at = 0;
+        for (int32_t L = 1; L <= r->depth; L++) {
+            r->level_begin[L] = (int32_t)at;
+            for (const RunItem &it : r->items) {
+                NetlistObj *n = find_netlist(c, it.netlist_id);
+                if (L > n->lv.depth) continue;
+                for (int32_t q = n->lv.level_begin[L]; q < n->lv.level_begin[L + 1]; q++) {
+                    GateRec g = n->recs[q];
+                    for (int k = 0; k < g.k; k++) g.fin[k] += (int32_t)it.net_base;
+                    g.out_net += (uint32_t)it.net_base;
+                    comb[at++] = g;
+                }
+            }
+        }
+        r->level_begin[r->depth + 1] = (int32_t)at;
+        r->level_begin[0] = 0;
+        rc = dalloc_n(c, &r->d_gates, comb.size());
+        if (rc) return rc;
+        r->owns_gates = true;
+        CK(cudaMemcpy(r->d_gates, comb.data(), sizeof(GateRec) * comb.size(), cudaMemcpyHostToDevice));
+    }
+    if (arena_events <= 0) {
+        // default: 256 words per stimulus transition plus 1 Mi, at most half
+        // of what is left of the budget (GLS_EOVERFLOW reports the demand)
+        uint64_t left = c->budget > c->used ? c->budget - c->used : 0;
+        uint64_t meta = (uint64_t)r->n_nets * 16 + (uint64_t)r->depth * 4 + 4096;
+        uint64_t cap = left > meta ? (left - meta) / 2 / 4 : 0;
+        uint64_t want = 256ull * (uint64_t)stim_events + (1ull << 20);
+        arena_events = (int64_t)std::min(cap, want);
+    }
+    const int64_t N = r->n_nets;
+    r->dev.arena_cap = (uint64_t)arena_events;
+    r->dev.n_pi = 0;
+    r->dev.n_gates = r->n_gates;
+    r->dev.wait_limit_ns = c->wait_limit_ns;
+    r->dev.withhold_gate = c->withhold_gate;
+    r->dev.seg_target = c->seg_target;
+    rc = dalloc_n(c, &r->dev.net_ptr, (size_t)std::max<int64_t>(N, 1));
+    if (!rc) rc = dalloc_n(c, &r->dev.net_len, (size_t)std::max<int64_t>(N, 1));
+    // padded by one slot line: readers round a waveform's end up to 4 words
+    if (!rc) rc = dalloc_n(c, &r->dev.arena, (size_t)arena_events + 2 * kSlotAlign);
+    if (!rc) rc = dalloc_n(c, &r->dev.arena_top, 1);
+    if (!rc) rc = dalloc_n(c, &r->dev.status, 1);
+    if (!rc) rc = dalloc_n(c, &r->dev.level_ctr, (size_t)r->depth + 1);
+    if (!rc) rc = dalloc_n(c, &r->dev.done, (size_t)std::max<int64_t>(N, 1));
+    if (!rc) rc = dalloc_n(c, &r->d_sum, 1);
+    if (rc) { free_run(c, r.get()); return rc; }
+    cudaError_t e = cudaEventCreate(&r->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
+    if (e != cudaSuccess) { free_run(c, r.get()); return fail(GLS_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e)); }
+    rc = build_run_graph(c, r.get());
+    if (rc) { free_run(c, r.get()); return rc; }
+    out = std::move(r);
+    return GLS_OK;
+}
+
+// Dense CSR of one instance of a run (its nets in caller order) into host memory.
+int read_item(gls_ctx *c, RunObj *r, int32_t item, int64_t *off, uint32_t *packed, int64_t cap) {
+    if (item < 0 || item >= (int32_t)r->items.size()) return fail(GLS_EINVAL, "item %d out of range", item);
+    const RunItem &it = r->items[item];
+    NetlistObj *n = find_netlist(c, it.netlist_id);
+    const int64_t N = (int64_t)n->n_pi + n->n_gates;
+    CK(cudaEventSynchronize(r->ev1));
+    int rc = GLS_OK;
+    if (r->off_cap < N + 1) {
+        dfree(c, r->d_off);
+        dfree(c, r->d_scan_tmp);
+        r->d_off = nullptr;
+        r->d_scan_tmp = nullptr;
+        r->off_cap = 0;
+        r->scan_tmp = scan_tmp_elems(N + 1);
+        rc = dalloc_n(c, &r->d_off, (size_t)N + 1);
+        if (!rc) rc = dalloc_n(c, &r->d_scan_tmp, r->scan_tmp);
+        if (rc) return rc;
+        r->off_cap = N + 1;
+    }
+    CK(launch_gather_lengths(r->dev.net_len, n->d_ext2int, N, r->d_off, c->stream, it.net_base));
+    CK(launch_exclusive_scan_i64(r->d_off, N + 1, r->d_scan_tmp, r->scan_tmp, c->stream));
+    CK(cudaMemcpyAsync(off, r->d_off, sizeof(int64_t) * (size_t)(N + 1), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int64_t total = off[N];
+    if (total > cap) return fail(GLS_EOVERFLOW, "%lld transitions, cap %lld", (long long)total, (long long)cap);
+    if (total == 0) return GLS_OK;
+    if (!packed) return fail(GLS_EINVAL, "NULL packed array");
+    if (total > r->gather_cap) {
+        dfree(c, r->d_gather);
+        r->d_gather = nullptr;
+        r->gather_cap = 0;
+        rc = dalloc_n(c, &r->d_gather, (size_t)total);
+        if (rc) return rc;
+        r->gather_cap = total;
+    }
+    CK(launch_gather_events(r->dev.net_ptr, r->dev.net_len, n->d_ext2int, r->d_off, N, r->d_gather, c->stream,
+                            it.net_base));
+    CK(cudaMemcpyAsync(packed, r->d_gather, sizeof(uint32_t) * (size_t)total, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return GLS_OK;
 }
 
@@ -556,6 +721,7 @@ int gls_load_netlist(gls_ctx *c, int32_t n_pi, int32_t n_gates, const uint8_t *t
         if (!rc) rc = dalloc_n(c, &n->d_ext2int, (size_t)std::max<int64_t>(N, 1));
         if (rc) { free_netlist(c, n.get()); return rc; }
         CK(cudaMemcpyAsync(n->d_gates, recs.data(), sizeof(GateRec) * recs.size(), cudaMemcpyHostToDevice, c->stream));
+        n->recs = recs;
         if (N > 0)
             CK(cudaMemcpyAsync(n->d_ext2int, n->ext2int.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->stream));
         CK(cudaStreamSynchronize(c->stream));
@@ -610,54 +776,20 @@ int gls_update_stimulus(gls_ctx *c, int32_t stim_id, const int64_t *off, const i
 
 int gls_simulate(gls_ctx *c, int32_t netlist_id, int32_t stim_id, int64_t arena_events, void *cuda_stream,
                  int32_t *run_id) {
-    if (!c || !run_id) return fail(GLS_EINVAL, "NULL argument");
+    return gls_simulate_batch(c, 1, &netlist_id, &stim_id, arena_events, cuda_stream, run_id);
+}
+
+int gls_simulate_batch(gls_ctx *c, int32_t n_items, const int32_t *netlist_ids, const int32_t *stim_ids,
+                       int64_t arena_events, void *cuda_stream, int32_t *run_id) {
+    if (!c || !run_id || !netlist_ids || !stim_ids) return fail(GLS_EINVAL, "NULL argument");
+    if (n_items < 1) return fail(GLS_EINVAL, "a run needs at least one item");
     try {
         CK(cudaSetDevice(c->device));
-        NetlistObj *n = find_netlist(c, netlist_id);
-        StimObj *s = find_stim(c, stim_id);
-        if (!n) return fail(GLS_EINVAL, "unknown netlist id %d", netlist_id);
-        if (!s) return fail(GLS_EINVAL, "unknown stimulus id %d", stim_id);
-        if (s->n_pi != n->n_pi) return fail(GLS_EINVAL, "stimulus has %d PIs, netlist %d", s->n_pi, n->n_pi);
-        int rc = time_range_check(n, s);
+        std::unique_ptr<RunObj> r;
+        int rc = create_run(c, netlist_ids, stim_ids, n_items, arena_events, r);
         if (rc) return rc;
-        const int64_t N = (int64_t)n->n_pi + n->n_gates;
-        if (arena_events <= 0) {
-            // default: 256 words per stimulus transition plus 1 Mi, at most half
-            // of what is left of the budget (GLS_EOVERFLOW reports the demand)
-            uint64_t left = c->budget > c->used ? c->budget - c->used : 0;
-            uint64_t meta = (uint64_t)N * 12 + (uint64_t)n->lv.depth * 4 + 4096;
-            uint64_t cap = left > meta ? (left - meta) / 2 / 4 : 0;
-            uint64_t want = 256ull * (uint64_t)s->n_events + (1ull << 20);
-            arena_events = (int64_t)std::min(cap, want);
-        }
-        auto r = std::make_unique<RunObj>();
-        r->netlist_id = netlist_id;
-        r->stim_id = stim_id;
-        r->dev.arena_cap = (uint64_t)arena_events;
-        r->dev.n_pi = n->n_pi;
-        r->dev.n_gates = n->n_gates;
-        r->dev.wait_limit_ns = c->wait_limit_ns;
-        r->dev.withhold_gate = c->withhold_gate;
-        r->dev.seg_target = c->seg_target;
-        r->schedule = c->schedule;
-        rc = dalloc_n(c, &r->dev.net_ptr, (size_t)std::max<int64_t>(N, 1));
-        if (!rc) rc = dalloc_n(c, &r->dev.net_len, (size_t)std::max<int64_t>(N, 1));
-        // padded by one slot line: readers round a waveform's end up to 4 words
-        if (!rc) rc = dalloc_n(c, &r->dev.arena, (size_t)arena_events + 2 * kSlotAlign);
-        if (!rc) rc = dalloc_n(c, &r->dev.arena_top, 1);
-        if (!rc) rc = dalloc_n(c, &r->dev.status, 1);
-        if (!rc) rc = dalloc_n(c, &r->dev.level_ctr, (size_t)n->lv.depth + 1);
-        if (!rc) rc = dalloc_n(c, &r->dev.done, (size_t)std::max(n->n_gates, 1));
-        if (!rc) rc = dalloc_n(c, &r->d_sum, 1);
-        if (rc) { free_run(c, r.get()); return rc; }
-        cudaError_t e = cudaEventCreate(&r->ev0);
-        if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
-        if (e != cudaSuccess) { free_run(c, r.get()); return fail(GLS_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e)); }
-        rc = build_run_graph(c, r.get(), n, s);
-        if (rc) { free_run(c, r.get()); return rc; }
-        e = cudaGraphLaunch(r->exec, pick_stream(c, cuda_stream));
+        cudaError_t e = cudaGraphLaunch(r->exec, pick_stream(c, cuda_stream));
         if (e != cudaSuccess) { free_run(c, r.get()); return fail(GLS_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e)); }
-        r->launched = true;
         const int32_t id = c->next_id++;
         c->runs[id] = std::move(r);
         *run_id = id;
@@ -671,10 +803,7 @@ int gls_rerun(gls_ctx *c, int32_t run_id, void *cuda_stream) {
     if (!c) return fail(GLS_EINVAL, "NULL context");
     RunObj *r = find_run(c, run_id);
     if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
-    NetlistObj *n = find_netlist(c, r->netlist_id);
-    StimObj *s = find_stim(c, r->stim_id);
-    if (!n || !s) return fail(GLS_EINVAL, "run %d lost its netlist or stimulus", run_id);
-    int rc = time_range_check(n, s);
+    int rc = items_time_range_check(c, r);
     if (rc) return rc;
     CK(cudaSetDevice(c->device));
     CK(cudaGraphLaunch(r->exec, pick_stream(c, cuda_stream)));
@@ -685,15 +814,16 @@ int gls_run_stats(gls_ctx *c, int32_t run_id, int64_t *total_events, double *ker
     if (!c) return fail(GLS_EINVAL, "NULL context");
     RunObj *r = find_run(c, run_id);
     if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
-    NetlistObj *n = find_netlist(c, r->netlist_id);
     CK(cudaSetDevice(c->device));
     CK(cudaEventSynchronize(r->ev1));
     uint32_t status = 0;
     unsigned long long top = 0, sum = 0;
     CK(cudaMemcpyAsync(&status, r->dev.status, sizeof status, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&top, r->dev.arena_top, sizeof top, cudaMemcpyDeviceToHost, c->stream));
-    const int64_t N = (int64_t)n->n_pi + n->n_gates;
-    CK(launch_sum_gate_lengths(r->dev.net_len, n->n_pi, N, r->d_sum, c->stream));
+    // every net, minus the primary inputs (the stimulus transitions)
+    CK(launch_sum_gate_lengths(r->dev.net_len, 0, r->n_nets, r->d_sum, c->stream));
+    unsigned long long pi_events = 0;
+    for (const RunItem &it : r->items) pi_events += (unsigned long long)find_stim(c, it.stim_id)->n_events;
     CK(cudaMemcpyAsync(&sum, r->d_sum, sizeof sum, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (kernel_ms) {
@@ -706,7 +836,7 @@ int gls_run_stats(gls_ctx *c, int32_t run_id, int64_t *total_events, double *ker
         return fail(GLS_EOVERFLOW, "event arena of %llu transitions too small; the run needs %llu",
                     (unsigned long long)r->dev.arena_cap, top);
     }
-    if (total_events) *total_events = (int64_t)sum;
+    if (total_events) *total_events = (int64_t)(sum - pi_events);
     if (status & kStPendingOverflow) return fail(GLS_ERANGE, "a cell's pending transitions exceeded the device buffer");
     if (status & kStTimeRange) return fail(GLS_ERANGE, "a computed time reached 2^30-1");
     if (status & kStTimeout) return fail(GLS_ETIMEOUT, "a wait for a fanin gate exceeded %.3f s",
@@ -718,12 +848,12 @@ int gls_read_waveform(gls_ctx *c, int32_t run_id, int32_t net, int32_t *t, uint8
     if (!c) return fail(GLS_EINVAL, "NULL context");
     RunObj *r = find_run(c, run_id);
     if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
-    NetlistObj *n = find_netlist(c, r->netlist_id);
+    NetlistObj *n = find_netlist(c, r->items[0].netlist_id);
     const int64_t N = (int64_t)n->n_pi + n->n_gates;
     if (net < 0 || net >= N) return fail(GLS_EINVAL, "net %d out of range", net);
     CK(cudaSetDevice(c->device));
     CK(cudaEventSynchronize(r->ev1));
-    const int32_t in = n->ext2int[net];
+    const int64_t in = r->items[0].net_base + n->ext2int[net];
     uint64_t ptr = 0;
     uint32_t len = 0;
     CK(cudaMemcpy(&ptr, r->dev.net_ptr + in, sizeof ptr, cudaMemcpyDeviceToHost));
@@ -746,40 +876,19 @@ int gls_read_waveform(gls_ctx *c, int32_t run_id, int32_t net, int32_t *t, uint8
 }
 
 int gls_read_all(gls_ctx *c, int32_t run_id, int64_t *off, uint32_t *packed, int64_t cap) {
+    return gls_read_item(c, run_id, 0, off, packed, cap);
+}
+
+int gls_read_item(gls_ctx *c, int32_t run_id, int32_t item, int64_t *off, uint32_t *packed, int64_t cap) {
     if (!c || !off) return fail(GLS_EINVAL, "NULL argument");
     RunObj *r = find_run(c, run_id);
     if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
-    NetlistObj *n = find_netlist(c, r->netlist_id);
-    const int64_t N = (int64_t)n->n_pi + n->n_gates;
     CK(cudaSetDevice(c->device));
-    CK(cudaEventSynchronize(r->ev1));
-    int rc = GLS_OK;
-    if (!r->d_off) {
-        r->scan_tmp = scan_tmp_elems(N + 1);
-        rc = dalloc_n(c, &r->d_off, (size_t)N + 1);
-        if (!rc) rc = dalloc_n(c, &r->d_scan_tmp, r->scan_tmp);
-        if (rc) return rc;
+    try {
+        return read_item(c, r, item, off, packed, cap);
+    } catch (const std::bad_alloc &) {
+        return fail(GLS_ENOMEM, "host allocation failed");
     }
-    CK(launch_gather_lengths(r->dev.net_len, n->d_ext2int, N, r->d_off, c->stream));
-    CK(launch_exclusive_scan_i64(r->d_off, N + 1, r->d_scan_tmp, r->scan_tmp, c->stream));
-    CK(cudaMemcpyAsync(off, r->d_off, sizeof(int64_t) * (size_t)(N + 1), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    const int64_t total = off[N];
-    if (total > cap) return fail(GLS_EOVERFLOW, "%lld transitions, cap %lld", (long long)total, (long long)cap);
-    if (total == 0) return GLS_OK;
-    if (!packed) return fail(GLS_EINVAL, "NULL packed array");
-    if (total > r->gather_cap) {
-        dfree(c, r->d_gather);
-        r->d_gather = nullptr;
-        r->gather_cap = 0;
-        rc = dalloc_n(c, &r->d_gather, (size_t)total);
-        if (rc) return rc;
-        r->gather_cap = total;
-    }
-    CK(launch_gather_events(r->dev.net_ptr, r->dev.net_len, n->d_ext2int, r->d_off, N, r->d_gather, c->stream));
-    CK(cudaMemcpyAsync(packed, r->d_gather, sizeof(uint32_t) * (size_t)total, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return GLS_OK;
 }
 
 int gls_set_option(gls_ctx *c, int option, int64_t value) {
@@ -876,8 +985,9 @@ int gls_release(gls_ctx *c, int32_t id) {
         return GLS_OK;
     }
     for (auto &kv : c->runs)
-        if (kv.second->netlist_id == id || kv.second->stim_id == id)
-            return fail(GLS_EINVAL, "id %d is still used by run %d", id, kv.first);
+        for (const RunItem &it : kv.second->items)
+            if (it.netlist_id == id || it.stim_id == id)
+                return fail(GLS_EINVAL, "id %d is still used by run %d", id, kv.first);
     if (auto it = c->stims.find(id); it != c->stims.end()) {
         free_stim(c, it->second.get());
         c->stims.erase(it);

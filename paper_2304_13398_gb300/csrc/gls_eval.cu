@@ -774,6 +774,8 @@ __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin,
 // Algorithm 1 without level barriers: gates are handed out in level order, so
 // every fanin gate of a handed-out gate was handed out earlier to a running
 // warp and the waits always end (the bound only guards against faults).
+// Completion flags are per net: primary inputs start done, a gate's output
+// net is released once its waveform and descriptor are written.
 template <int V>
 __global__ void dependency_kernel(const GateRec *__restrict__ gates, int32_t n_gates, int32_t ctr_slot, RunDev r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -785,8 +787,8 @@ __global__ void dependency_kernel(const GateRec *__restrict__ gates, int32_t n_g
         if (g >= n_gates) break;
         const GateRec gr = gates[g];
         bool ok = true;
-        if (lane < gr.k && gr.fin[lane] >= r.n_pi) {
-            const uint32_t *flag = r.done + (gr.fin[lane] - r.n_pi);
+        if (lane < gr.k) {   // primary-input flags are set before the launch
+            const uint32_t *flag = r.done + gr.fin[lane];
             if (ld_acquire(flag) == 0u) {
                 const uint64_t t0 = globaltimer();
                 while (ld_acquire(flag) == 0u) {
@@ -805,7 +807,7 @@ __global__ void dependency_kernel(const GateRec *__restrict__ gates, int32_t n_g
         }
         __threadfence();
         __syncwarp();
-        if (lane == 0 && g != r.withhold_gate) st_release(r.done + (gr.out_net - r.n_pi), 1u);
+        if (lane == 0 && g != r.withhold_gate) st_release(r.done + gr.out_net, 1u);
     }
 }
 

@@ -42,7 +42,7 @@ struct RunDev {
     unsigned long long *arena_top;  // bump pointer (transitions), counts demand past cap
     uint32_t *status;         // kSt* bits
     int32_t *level_ctr;       // [depth + 1] work counters, zeroed per run (last: dependency mode)
-    uint32_t *done;           // [G] per-gate completion flags (dependency mode), zeroed per run
+    uint32_t *done;           // [N] per-net completion flags (dependency mode): PIs 1, gates 0 per run
     int32_t n_pi;
     int32_t n_gates;
     uint64_t wait_limit_ns;   // bound on one wait for a fanin (dependency mode)
@@ -93,13 +93,19 @@ cudaError_t launch_pack_stimulus(const int64_t *d_off, const int32_t *d_t, const
                                  uint32_t *d_packed, uint32_t *d_status, cudaStream_t s);
 cudaError_t launch_run_init(const int64_t *d_stim_off, const uint32_t *d_stim_packed, const RunDev &r,
                             int32_t n_ctr, cudaStream_t s);
+// primary-input descriptors (and completion flags) of one instance whose nets
+// start at net_base
+cudaError_t launch_pi_init(const int64_t *d_stim_off, const uint32_t *d_stim_packed, int32_t n_pi, int64_t net_base,
+                           uint64_t *net_ptr, uint32_t *net_len, uint32_t *done, cudaStream_t s);
+// gather of nets net_base + ext2int[i], i < n
 cudaError_t launch_gather_lengths(const uint32_t *d_net_len, const int32_t *d_ext2int, int64_t n,
-                                  int64_t *d_off, cudaStream_t s);
+                                  int64_t *d_off, cudaStream_t s, int64_t net_base = 0);
 cudaError_t launch_exclusive_scan_i64(int64_t *d_data, int64_t n, int64_t *d_tmp, size_t tmp_elems,
                                       cudaStream_t s);
 size_t scan_tmp_elems(int64_t n);
 cudaError_t launch_gather_events(const uint64_t *d_net_ptr, const uint32_t *d_net_len, const int32_t *d_ext2int,
-                                 const int64_t *d_off, int64_t n, uint32_t *d_out, cudaStream_t s);
+                                 const int64_t *d_off, int64_t n, uint32_t *d_out, cudaStream_t s,
+                                 int64_t net_base = 0);
 cudaError_t launch_sum_gate_lengths(const uint32_t *d_net_len, int32_t n_pi, int64_t n, unsigned long long *d_sum,
                                     cudaStream_t s);
 

@@ -54,11 +54,24 @@ __global__ void run_init_kernel(const int64_t *__restrict__ off, const uint32_t 
     if (tid == 0) { *r.arena_top = 0; *r.status = 0; }
 }
 
+// Descriptors of one instance's primary inputs (nets net_base + i) and, in
+// the dependency schedule, their completion flags.
+__global__ void pi_init_kernel(const int64_t *__restrict__ off, const uint32_t *packed, int32_t n_pi, int64_t net_base,
+                               uint64_t *net_ptr, uint32_t *net_len, uint32_t *done) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pi; i += stride) {
+        const int64_t a = off[i];
+        net_ptr[net_base + i] = reinterpret_cast<uint64_t>(packed + stim_slot(a, i));
+        net_len[net_base + i] = (uint32_t)(off[i + 1] - a);
+        if (done) done[net_base + i] = 1u;
+    }
+}
+
 __global__ void gather_lengths_kernel(const uint32_t *__restrict__ net_len, const int32_t *__restrict__ ext2int,
-                                      int64_t n, int64_t *__restrict__ off) {
+                                      int64_t n, int64_t *__restrict__ off, int64_t net_base) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride)
-        off[i] = i < n ? (int64_t)net_len[ext2int[i]] : 0;
+        off[i] = i < n ? (int64_t)net_len[net_base + ext2int[i]] : 0;
 }
 
 constexpr int SCAN_T = 512;            // threads per scan block
@@ -117,11 +130,11 @@ __global__ void scan_add_kernel(int64_t *data, int64_t n, const int64_t *offs) {
 // dense CSR position.
 __global__ void gather_events_kernel(const uint64_t *__restrict__ net_ptr, const uint32_t *__restrict__ net_len,
                                      const int32_t *__restrict__ ext2int, const int64_t *__restrict__ off, int64_t n,
-                                     uint32_t *__restrict__ out) {
+                                     uint32_t *__restrict__ out, int64_t net_base) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
-        const int32_t in = ext2int[i];
+        const int64_t in = net_base + ext2int[i];
         const uint32_t len = net_len[in];
         const uint32_t *src = reinterpret_cast<const uint32_t *>(net_ptr[in]);
         uint32_t *dst = out + off[i];
@@ -163,9 +176,16 @@ cudaError_t launch_run_init(const int64_t *d_stim_off, const uint32_t *d_stim_pa
     return cudaGetLastError();
 }
 
+cudaError_t launch_pi_init(const int64_t *d_stim_off, const uint32_t *d_stim_packed, int32_t n_pi, int64_t net_base,
+                           uint64_t *net_ptr, uint32_t *net_len, uint32_t *done, cudaStream_t s) {
+    if (n_pi <= 0) return cudaSuccess;
+    pi_init_kernel<<<grid_for(n_pi, 256), 256, 0, s>>>(d_stim_off, d_stim_packed, n_pi, net_base, net_ptr, net_len, done);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather_lengths(const uint32_t *d_net_len, const int32_t *d_ext2int, int64_t n, int64_t *d_off,
-                                  cudaStream_t s) {
-    gather_lengths_kernel<<<grid_for(n + 1, 256), 256, 0, s>>>(d_net_len, d_ext2int, n, d_off);
+                                  cudaStream_t s, int64_t net_base) {
+    gather_lengths_kernel<<<grid_for(n + 1, 256), 256, 0, s>>>(d_net_len, d_ext2int, n, d_off, net_base);
     return cudaGetLastError();
 }
 
@@ -195,9 +215,9 @@ cudaError_t launch_exclusive_scan_i64(int64_t *d_data, int64_t n, int64_t *d_tmp
 }
 
 cudaError_t launch_gather_events(const uint64_t *d_net_ptr, const uint32_t *d_net_len, const int32_t *d_ext2int,
-                                 const int64_t *d_off, int64_t n, uint32_t *d_out, cudaStream_t s) {
+                                 const int64_t *d_off, int64_t n, uint32_t *d_out, cudaStream_t s, int64_t net_base) {
     if (n <= 0) return cudaSuccess;
-    gather_events_kernel<<<grid_for(n, 8), 256, 0, s>>>(d_net_ptr, d_net_len, d_ext2int, d_off, n, d_out);
+    gather_events_kernel<<<grid_for(n, 8), 256, 0, s>>>(d_net_ptr, d_net_len, d_ext2int, d_off, n, d_out, net_base);
     return cudaGetLastError();
 }
 

@@ -41,10 +41,12 @@ SIGNATURES = [
     ("gls_load_stimulus", ctypes.c_int, [P, i32, P, P, P, ctypes.POINTER(i32)]),
     ("gls_update_stimulus", ctypes.c_int, [P, i32, P, P, P]),
     ("gls_simulate", ctypes.c_int, [P, i32, i32, i64, P, ctypes.POINTER(i32)]),
+    ("gls_simulate_batch", ctypes.c_int, [P, i32, P, P, i64, P, ctypes.POINTER(i32)]),
     ("gls_rerun", ctypes.c_int, [P, i32, P]),
     ("gls_run_stats", ctypes.c_int, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]),
     ("gls_read_waveform", ctypes.c_int, [P, i32, i32, P, P, i64, ctypes.POINTER(i64)]),
     ("gls_read_all", ctypes.c_int, [P, i32, P, P, i64]),
+    ("gls_read_item", ctypes.c_int, [P, i32, i32, P, P, i64]),
     ("gls_set_option", ctypes.c_int, [P, ctypes.c_int, i64]),
     ("gls_simulate_noalloc", ctypes.c_int, [P, i32, i32, P, P, P, i64, P, P]),
     ("gls_release", ctypes.c_int, [P, i32]),
@@ -205,6 +207,34 @@ class Context:
         self.n_nets[rid.value] = self.n_nets[netlist_id]
         return rid.value
 
+    def simulate_batch(self, netlist_ids, stim_ids, arena_events: int = 0, stream=None) -> int:
+        """One launch over several (netlist, stimulus) items; read each with read_item."""
+        nids = _c(netlist_ids, np.int32)
+        sids = _c(stim_ids, np.int32)
+        if len(nids) != len(sids):
+            raise ValueError("netlist_ids and stim_ids differ in length")
+        rid = ctypes.c_int32(0)
+        self._ck(self.lib.gls_simulate_batch(self.h, len(nids), _p(nids), _p(sids), arena_events,
+                                             _stream_handle(stream), ctypes.byref(rid)))
+        self.n_nets[rid.value] = [self.n_nets[int(n)] for n in nids]
+        return rid.value
+
+    def read_item(self, run_id: int, item: int, off=None, packed=None):
+        """Dense CSR of one item of a batch run (see read_all)."""
+        nn = self.n_nets[run_id]
+        nn = nn if isinstance(nn, list) else [nn]
+        N = nn[item] if 0 <= item < len(nn) else 0   # the library rejects a bad item
+        if off is None:
+            off = np.zeros(N + 1, np.int64)
+        if packed is None:
+            rc = self.lib.gls_read_item(self.h, run_id, item, _ptr(off, np.int64), None, 0)
+            if rc not in (GLS_OK, GLS_EOVERFLOW):
+                self._ck(rc)
+            packed = np.zeros(int(off[N]), np.uint32)
+        cap = int(packed.shape[0]) if hasattr(packed, "shape") else len(packed)
+        self._ck(self.lib.gls_read_item(self.h, run_id, item, _ptr(off, np.int64), _ptr(packed, np.uint32), cap))
+        return off, packed
+
     def rerun(self, run_id: int, stream=None):
         self._ck(self.lib.gls_rerun(self.h, run_id, _stream_handle(stream)))
 
@@ -233,6 +263,7 @@ class Context:
         """Dense CSR of every net: (off int64[N+1], packed uint32[E]) with
         packed = (t << 2) | v.  Optional preallocated (pinned) outputs."""
         N = self.n_nets[run_id]
+        N = N[0] if isinstance(N, list) else N
         if off is None:
             off = np.zeros(N + 1, np.int64)
         if packed is None:
