@@ -169,14 +169,19 @@ int gls_simulate(gls_ctx *ctx, int32_t netlist_id, int32_t stim_id, int64_t aren
  * into one work order, so the dependency schedule's single persistent launch
  * (or one launch per level) covers every item and the long gates of one item
  * overlap with the work of the others.  netlist_ids[n_items] and
- * stim_ids[n_items] are loaded handles; arena_events as in gls_simulate
- * (0 = 256 words per stimulus transition of all items plus 2^20, capped at
- * half the unused budget).  Read items back with gls_read_item; gls_run_stats
- * reports all items together.  No counterpart in the paper (Sec. 4 simulates
- * one netlist at a time); each item's waveforms equal a gls_simulate of it.
+ * stim_ids[n_items] are loaded handles; items that all name one netlist are
+ * evaluated from that netlist's records without a copy.  t_limits[n_items]
+ * (NULL = none) keeps only the stimulus transitions before t_limits[i] in
+ * item i, i.e. simulates the first t_limits[i] ps of the given waveforms
+ * (a request window over a resident stimulus).  arena_events as in
+ * gls_simulate (0 = 256 words per stimulus transition of all items plus 2^20,
+ * capped at half the unused budget).  Read items back with gls_read_item;
+ * gls_run_stats reports all items together.  No counterpart in the paper
+ * (Sec. 4 simulates one netlist at a time); each item's waveforms equal a
+ * gls_simulate of it (with its stimulus cut at its time limit).
  */
 int gls_simulate_batch(gls_ctx *ctx, int32_t n_items, const int32_t *netlist_ids, const int32_t *stim_ids,
-                       int64_t arena_events, void *cuda_stream, int32_t *run_id);
+                       const int32_t *t_limits, int64_t arena_events, void *cuda_stream, int32_t *run_id);
 
 /* Enqueue the same run again (same buffers, current stimulus contents). */
 int gls_rerun(gls_ctx *ctx, int32_t run_id, void *cuda_stream);

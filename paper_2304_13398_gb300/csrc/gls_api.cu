@@ -215,6 +215,7 @@ struct NetlistObj {
     int32_t *d_ext2int = nullptr;      // [N] caller net id -> internal net id
     std::vector<int32_t> ext2int;      // host copy
     std::vector<GateRec> recs;         // host copy of the level-ordered records (batches)
+    int32_t *d_level_begin = nullptr;  // [depth + 2] device copy of lv.level_begin (replicated items)
 };
 
 struct StimObj {
@@ -232,6 +233,7 @@ struct StimObj {
 struct RunItem {
     int32_t netlist_id = 0, stim_id = 0;
     int64_t net_base = 0;
+    uint32_t t_limit = kTimeInf;       // stimulus transitions at or after this time are left out
 };
 
 struct RunObj {
@@ -246,6 +248,7 @@ struct RunObj {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     unsigned long long *d_sum = nullptr;
+    unsigned long long *d_pi_total = nullptr;
     int64_t *d_off = nullptr;          // [max nets + 1] for read-back
     int64_t off_cap = 0;
     int64_t *d_scan_tmp = nullptr;
@@ -315,6 +318,7 @@ void dfree(gls_ctx *c, void *p) {
 void free_netlist(gls_ctx *c, NetlistObj *n) {
     dfree(c, n->d_gates);
     dfree(c, n->d_ext2int);
+    dfree(c, n->d_level_begin);
 }
 void free_stim(gls_ctx *c, StimObj *s) {
     dfree(c, s->d_off);
@@ -335,6 +339,7 @@ void free_run(gls_ctx *c, RunObj *r) {
     dfree(c, r->dev.level_ctr);
     dfree(c, r->dev.done);
     dfree(c, r->d_sum);
+    dfree(c, r->d_pi_total);
     dfree(c, r->d_off);
     dfree(c, r->d_scan_tmp);
     dfree(c, r->d_gather);
@@ -387,12 +392,13 @@ int build_run_graph(gls_ctx *c, RunObj *r) {
     if (e == cudaSuccess) e = cudaMemsetAsync(r->dev.arena_top, 0, sizeof(unsigned long long), cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->dev.status, 0, sizeof(uint32_t), cs);
     if (e == cudaSuccess && dep) e = cudaMemsetAsync(r->dev.done, 0, sizeof(uint32_t) * (size_t)r->n_nets, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_pi_total, 0, sizeof(unsigned long long), cs);
     for (const RunItem &it : r->items) {
         if (e != cudaSuccess) break;
         NetlistObj *n = find_netlist(c, it.netlist_id);
         StimObj *s = find_stim(c, it.stim_id);
-        e = launch_pi_init(s->d_off, s->d_packed, n->n_pi, it.net_base, r->dev.net_ptr, r->dev.net_len,
-                           dep ? r->dev.done : nullptr, cs);
+        e = launch_pi_init(s->d_off, s->d_packed, n->n_pi, it.net_base, it.t_limit, r->dev.net_ptr, r->dev.net_len,
+                           dep ? r->dev.done : nullptr, r->d_pi_total, cs);
     }
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(r->ev0, cs, cudaEventRecordExternal);
     if (dep) {
@@ -442,8 +448,8 @@ int items_time_range_check(gls_ctx *c, const RunObj *r) {
 
 // Validate the instances, lay out their nets and gates, allocate the store and
 // capture the run's graph; the run is launched by the caller.
-int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, int32_t n_items,
-               int64_t arena_events, std::unique_ptr<RunObj> &out) {
+int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, const int32_t *t_limits,
+               int32_t n_items, int64_t arena_events, std::unique_ptr<RunObj> &out) {
     auto r = std::make_unique<RunObj>();
     r->schedule = c->schedule;
     int64_t stim_events = 0, base = 0;
@@ -455,7 +461,12 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
         if (s->n_pi != n->n_pi) return fail(GLS_EINVAL, "item %d: stimulus has %d PIs, netlist %d", i, s->n_pi, n->n_pi);
         int rc = time_range_check(n, s);
         if (rc) return rc;
-        r->items.push_back(RunItem{netlist_ids[i], stim_ids[i], base});
+        uint32_t tl = kTimeInf;
+        if (t_limits) {
+            if (t_limits[i] < 0) return fail(GLS_EINVAL, "item %d: negative time limit", i);
+            tl = (uint32_t)t_limits[i];
+        }
+        r->items.push_back(RunItem{netlist_ids[i], stim_ids[i], base, tl});
         base += (int64_t)n->n_pi + n->n_gates;
         r->n_gates += n->n_gates;
         r->depth = std::max(r->depth, n->lv.depth);
@@ -464,11 +475,17 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
     if (base >= (int64_t)INT32_MAX) return fail(GLS_EINVAL, "a run holds at most 2^31 - 1 nets");
     r->n_nets = base;
     int rc = GLS_OK;
-    if (n_items == 1) {   // one instance: its own records and levels
+    bool same = true;
+    for (int32_t i = 1; i < n_items; i++) same &= netlist_ids[i] == netlist_ids[0];
+    if (same) {   // one netlist (once or replicated): its own records, decoded per replica on the device
         NetlistObj *n = find_netlist(c, netlist_ids[0]);
         r->d_gates = n->d_gates;
         r->level_begin = n->lv.level_begin;
-    } else {              // records of all instances interleaved by level, net ids shifted
+        for (int32_t &x : r->level_begin) x *= n_items;
+        r->dev.rep = n_items;
+        r->dev.rep_nets = (int64_t)n->n_pi + n->n_gates;
+        r->dev.lb = n->d_level_begin;
+    } else {      // records of all instances interleaved by level, net ids shifted
         std::vector<GateRec> comb((size_t)std::max(r->n_gates, 1));
         r->level_begin.assign(r->depth + 2, 0);
         size_t at = 0;
@@ -517,7 +534,9 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
     if (!rc) rc = dalloc_n(c, &r->dev.level_ctr, (size_t)r->depth + 1);
     if (!rc) rc = dalloc_n(c, &r->dev.done, (size_t)std::max<int64_t>(N, 1));
     if (!rc) rc = dalloc_n(c, &r->d_sum, 1);
+    if (!rc) rc = dalloc_n(c, &r->d_pi_total, 1);
     if (rc) { free_run(c, r.get()); return rc; }
+    r->dev.pi_total = r->d_pi_total;
     cudaError_t e = cudaEventCreate(&r->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
     if (e != cudaSuccess) { free_run(c, r.get()); return fail(GLS_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e)); }
@@ -719,7 +738,10 @@ int gls_load_netlist(gls_ctx *c, int32_t n_pi, int32_t n_gates, const uint8_t *t
         for (int32_t g = 0; g < n_gates; g++) n->ext2int[n_pi + g] = n_pi + n->lv.pos[g];
         rc = dalloc_n(c, &n->d_gates, recs.size());
         if (!rc) rc = dalloc_n(c, &n->d_ext2int, (size_t)std::max<int64_t>(N, 1));
+        if (!rc) rc = dalloc_n(c, &n->d_level_begin, n->lv.level_begin.size());
         if (rc) { free_netlist(c, n.get()); return rc; }
+        CK(cudaMemcpyAsync(n->d_level_begin, n->lv.level_begin.data(), sizeof(int32_t) * n->lv.level_begin.size(),
+                           cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(n->d_gates, recs.data(), sizeof(GateRec) * recs.size(), cudaMemcpyHostToDevice, c->stream));
         n->recs = recs;
         if (N > 0)
@@ -776,17 +798,17 @@ int gls_update_stimulus(gls_ctx *c, int32_t stim_id, const int64_t *off, const i
 
 int gls_simulate(gls_ctx *c, int32_t netlist_id, int32_t stim_id, int64_t arena_events, void *cuda_stream,
                  int32_t *run_id) {
-    return gls_simulate_batch(c, 1, &netlist_id, &stim_id, arena_events, cuda_stream, run_id);
+    return gls_simulate_batch(c, 1, &netlist_id, &stim_id, nullptr, arena_events, cuda_stream, run_id);
 }
 
 int gls_simulate_batch(gls_ctx *c, int32_t n_items, const int32_t *netlist_ids, const int32_t *stim_ids,
-                       int64_t arena_events, void *cuda_stream, int32_t *run_id) {
+                       const int32_t *t_limits, int64_t arena_events, void *cuda_stream, int32_t *run_id) {
     if (!c || !run_id || !netlist_ids || !stim_ids) return fail(GLS_EINVAL, "NULL argument");
     if (n_items < 1) return fail(GLS_EINVAL, "a run needs at least one item");
     try {
         CK(cudaSetDevice(c->device));
         std::unique_ptr<RunObj> r;
-        int rc = create_run(c, netlist_ids, stim_ids, n_items, arena_events, r);
+        int rc = create_run(c, netlist_ids, stim_ids, t_limits, n_items, arena_events, r);
         if (rc) return rc;
         cudaError_t e = cudaGraphLaunch(r->exec, pick_stream(c, cuda_stream));
         if (e != cudaSuccess) { free_run(c, r.get()); return fail(GLS_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e)); }
@@ -820,10 +842,10 @@ int gls_run_stats(gls_ctx *c, int32_t run_id, int64_t *total_events, double *ker
     unsigned long long top = 0, sum = 0;
     CK(cudaMemcpyAsync(&status, r->dev.status, sizeof status, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&top, r->dev.arena_top, sizeof top, cudaMemcpyDeviceToHost, c->stream));
-    // every net, minus the primary inputs (the stimulus transitions)
+    // every net, minus the primary inputs (their transitions within the time limits)
     CK(launch_sum_gate_lengths(r->dev.net_len, 0, r->n_nets, r->d_sum, c->stream));
     unsigned long long pi_events = 0;
-    for (const RunItem &it : r->items) pi_events += (unsigned long long)find_stim(c, it.stim_id)->n_events;
+    CK(cudaMemcpyAsync(&pi_events, r->d_pi_total, sizeof pi_events, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&sum, r->d_sum, sizeof sum, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (kernel_ms) {

@@ -755,17 +755,37 @@ __device__ __forceinline__ void eval_variant(const GateRec &gr, const RunDev &r,
     else eval_windowed<DEP, 128>(gr, r, reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane);
 }
 
+// Gate record of work index g.  With rep > 1 replicas of one netlist the work
+// order is level by level and, inside a level, replica by replica; L is the
+// caller's running level hint (work indices only grow per warp) and the net
+// ids of replica i are shifted by i * rep_nets.
+__device__ __forceinline__ GateRec fetch_gate(const GateRec *__restrict__ gates, const RunDev &r, int64_t g,
+                                              int32_t &L) {
+    if (r.rep <= 1) return gates[g];
+    while (g >= (int64_t)r.rep * __ldg(r.lb + L + 1)) L++;
+    const int32_t b = __ldg(r.lb + L), cnt = __ldg(r.lb + L + 1) - b;
+    const int64_t off = g - (int64_t)r.rep * b;
+    const int64_t item = off / cnt;
+    GateRec gr = gates[b + (int32_t)(off - item * cnt)];
+    const int32_t sh = (int32_t)(item * r.rep_nets);
+#pragma unroll
+    for (int k = 0; k < 3; k++) gr.fin[k] += sh;
+    gr.out_net += (uint32_t)sh;
+    return gr;
+}
+
 template <int V>
 __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin, int32_t g_count,
                              int32_t level, RunDev r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t L = level + 1;
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(r.level_ctr + level, 1);
         g = __shfl_sync(FULL, g, 0);
         if (g >= g_count) break;
-        const GateRec gr = gates[g_begin + g];
+        const GateRec gr = fetch_gate(gates, r, (int64_t)g_begin + g, L);
         eval_variant<V, false>(gr, r, smem_raw, warp, lane);
         __syncwarp();
     }
@@ -780,12 +800,13 @@ template <int V>
 __global__ void dependency_kernel(const GateRec *__restrict__ gates, int32_t n_gates, int32_t ctr_slot, RunDev r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t L = 1;
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(r.level_ctr + ctr_slot, 1);
         g = __shfl_sync(FULL, g, 0);
         if (g >= n_gates) break;
-        const GateRec gr = gates[g];
+        const GateRec gr = fetch_gate(gates, r, g, L);
         bool ok = true;
         if (lane < gr.k) {   // primary-input flags are set before the launch
             const uint32_t *flag = r.done + gr.fin[lane];

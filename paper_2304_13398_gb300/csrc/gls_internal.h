@@ -48,6 +48,13 @@ struct RunDev {
     uint64_t wait_limit_ns;   // bound on one wait for a fanin (dependency mode)
     int32_t withhold_gate;    // test hook: this gate never publishes its flag (-1: none)
     uint32_t seg_target;      // segmented variant: target transitions per lane segment
+    // replicated items: rep > 1 instances of one netlist (level_begin lb[],
+    // rep_nets nets each) are evaluated without a copy of its gate records;
+    // work index g -> (level L, replica, gate) level by level, replica by replica
+    int32_t rep;
+    int64_t rep_nets;
+    const int32_t *lb;
+    unsigned long long *pi_total;   // primary-input transitions of the run (after time limits)
 };
 
 // Output slots are padded to whole 128-byte lines so that no two nets share a
@@ -95,8 +102,10 @@ cudaError_t launch_run_init(const int64_t *d_stim_off, const uint32_t *d_stim_pa
                             int32_t n_ctr, cudaStream_t s);
 // primary-input descriptors (and completion flags) of one instance whose nets
 // start at net_base
+// (transitions at or after t_limit are left out of the instance)
 cudaError_t launch_pi_init(const int64_t *d_stim_off, const uint32_t *d_stim_packed, int32_t n_pi, int64_t net_base,
-                           uint64_t *net_ptr, uint32_t *net_len, uint32_t *done, cudaStream_t s);
+                           uint32_t t_limit, uint64_t *net_ptr, uint32_t *net_len, uint32_t *done,
+                           unsigned long long *pi_total, cudaStream_t s);
 // gather of nets net_base + ext2int[i], i < n
 cudaError_t launch_gather_lengths(const uint32_t *d_net_len, const int32_t *d_ext2int, int64_t n,
                                   int64_t *d_off, cudaStream_t s, int64_t net_base = 0);

@@ -55,16 +55,31 @@ __global__ void run_init_kernel(const int64_t *__restrict__ off, const uint32_t 
 }
 
 // Descriptors of one instance's primary inputs (nets net_base + i) and, in
-// the dependency schedule, their completion flags.
+// the dependency schedule, their completion flags.  Only transitions before
+// t_limit belong to the instance (a prefix of each waveform).
 __global__ void pi_init_kernel(const int64_t *__restrict__ off, const uint32_t *packed, int32_t n_pi, int64_t net_base,
-                               uint64_t *net_ptr, uint32_t *net_len, uint32_t *done) {
+                               uint32_t t_limit, uint64_t *net_ptr, uint32_t *net_len, uint32_t *done,
+                               unsigned long long *pi_total) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long tot = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pi; i += stride) {
         const int64_t a = off[i];
-        net_ptr[net_base + i] = reinterpret_cast<uint64_t>(packed + stim_slot(a, i));
-        net_len[net_base + i] = (uint32_t)(off[i + 1] - a);
+        const uint32_t *w = packed + stim_slot(a, i);
+        uint32_t lo = 0, hi = (uint32_t)(off[i + 1] - a);
+        if (t_limit != kTimeInf)
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if ((w[mid] >> 2) < t_limit) lo = mid + 1;
+                else hi = mid;
+            }
+        else lo = hi;
+        net_ptr[net_base + i] = reinterpret_cast<uint64_t>(w);
+        net_len[net_base + i] = lo;
         if (done) done[net_base + i] = 1u;
+        tot += lo;
     }
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULL, tot, o);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(pi_total, tot);
 }
 
 __global__ void gather_lengths_kernel(const uint32_t *__restrict__ net_len, const int32_t *__restrict__ ext2int,
@@ -177,9 +192,11 @@ cudaError_t launch_run_init(const int64_t *d_stim_off, const uint32_t *d_stim_pa
 }
 
 cudaError_t launch_pi_init(const int64_t *d_stim_off, const uint32_t *d_stim_packed, int32_t n_pi, int64_t net_base,
-                           uint64_t *net_ptr, uint32_t *net_len, uint32_t *done, cudaStream_t s) {
+                           uint32_t t_limit, uint64_t *net_ptr, uint32_t *net_len, uint32_t *done,
+                           unsigned long long *pi_total, cudaStream_t s) {
     if (n_pi <= 0) return cudaSuccess;
-    pi_init_kernel<<<grid_for(n_pi, 256), 256, 0, s>>>(d_stim_off, d_stim_packed, n_pi, net_base, net_ptr, net_len, done);
+    pi_init_kernel<<<grid_for(n_pi, 256), 256, 0, s>>>(d_stim_off, d_stim_packed, n_pi, net_base, t_limit, net_ptr,
+                                                         net_len, done, pi_total);
     return cudaGetLastError();
 }
 

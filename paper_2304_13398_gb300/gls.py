@@ -41,7 +41,7 @@ SIGNATURES = [
     ("gls_load_stimulus", ctypes.c_int, [P, i32, P, P, P, ctypes.POINTER(i32)]),
     ("gls_update_stimulus", ctypes.c_int, [P, i32, P, P, P]),
     ("gls_simulate", ctypes.c_int, [P, i32, i32, i64, P, ctypes.POINTER(i32)]),
-    ("gls_simulate_batch", ctypes.c_int, [P, i32, P, P, i64, P, ctypes.POINTER(i32)]),
+    ("gls_simulate_batch", ctypes.c_int, [P, i32, P, P, P, i64, P, ctypes.POINTER(i32)]),
     ("gls_rerun", ctypes.c_int, [P, i32, P]),
     ("gls_run_stats", ctypes.c_int, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]),
     ("gls_read_waveform", ctypes.c_int, [P, i32, i32, P, P, i64, ctypes.POINTER(i64)]),
@@ -207,14 +207,15 @@ class Context:
         self.n_nets[rid.value] = self.n_nets[netlist_id]
         return rid.value
 
-    def simulate_batch(self, netlist_ids, stim_ids, arena_events: int = 0, stream=None) -> int:
-        """One launch over several (netlist, stimulus) items; read each with read_item."""
+    def simulate_batch(self, netlist_ids, stim_ids, t_limits=None, arena_events: int = 0, stream=None) -> int:
+        """One launch over several (netlist, stimulus[, time limit]) items; read each with read_item."""
         nids = _c(netlist_ids, np.int32)
         sids = _c(stim_ids, np.int32)
-        if len(nids) != len(sids):
-            raise ValueError("netlist_ids and stim_ids differ in length")
+        tls = None if t_limits is None else _c(t_limits, np.int32)
+        if len(nids) != len(sids) or (tls is not None and len(tls) != len(nids)):
+            raise ValueError("item arrays differ in length")
         rid = ctypes.c_int32(0)
-        self._ck(self.lib.gls_simulate_batch(self.h, len(nids), _p(nids), _p(sids), arena_events,
+        self._ck(self.lib.gls_simulate_batch(self.h, len(nids), _p(nids), _p(sids), _p(tls), arena_events,
                                              _stream_handle(stream), ctypes.byref(rid)))
         self.n_nets[rid.value] = [self.n_nets[int(n)] for n in nids]
         return rid.value

@@ -85,3 +85,37 @@ def test_batch_errors():
             ctx.read_item(rid, 2)
         with pytest.raises(gls.GlsError):
             ctx.release(sid)                                  # still used by the batch
+
+
+def _cut(st, t_limit):
+    """stimulus restricted to transitions before t_limit (oracle-side reference)"""
+    keep = st.t < t_limit
+    lens = np.diff(st.off)
+    per = np.add.reduceat(keep.astype(np.int64), st.off[:-1]) if len(st.t) else np.zeros(len(lens), np.int64)
+    per = np.where(lens > 0, per, 0)
+    off = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(per, out=off[1:])
+    return synth.Stimulus(off, st.t[keep], st.v[keep])
+
+
+@pytest.mark.parametrize("schedule", ["dependency", "levels"])
+def test_replicas_with_time_limits(schedule):
+    nl = synth.make_netlist(10, 600, 12, fanout="pareto", d_min=5, d_max=200, seed=77)
+    stims = [synth.make_stimulus(10, mean=300, window=100_000, seed=300 + s) for s in range(3)]
+    plan = [(0, None), (1, 40_000), (0, 1), (2, 99_999), (1, 0), (2, 7_777), (0, 55_555)]
+    with gls.Context(0) as ctx:
+        ctx.set_schedule(schedule)
+        nid = ctx.load_netlist(nl)
+        sids = [ctx.load_stimulus(st) for st in stims]
+        limits = [(1 << 30) - 2 if t is None else t for _, t in plan]
+        rid = ctx.simulate_batch([nid] * len(plan), [sids[k] for k, _ in plan], t_limits=limits)
+        stats = ctx.run_stats(rid)
+        total = 0
+        for i, (k, t) in enumerate(plan):
+            st = stims[k] if t is None else _cut(stims[k], t)
+            ref = oracle.sim_event(nl, st)
+            off, packed = ctx.read_item(rid, i)
+            tt, vv = gls.unpack(packed)
+            assert_same(ref, off, tt, vv, f"replica {i} (stimulus {k}, limit {t})")
+            total += int(ref.off[-1] - ref.off[nl.n_pi])
+        assert stats.total_events == total
