@@ -56,7 +56,8 @@ typedef enum gls_status {
     GLS_ENOMEM = -5,     /* device or host allocation failed / budget exceeded     */
     GLS_EOVERFLOW = -6,  /* output larger than the given capacity or run arena     */
     GLS_ETIMEOUT = -7,   /* a bounded device wait gave up                          */
-    GLS_ECUDA = -8       /* CUDA runtime error                                     */
+    GLS_ECUDA = -8,      /* CUDA runtime error                                     */
+    GLS_EAGAIN = -9      /* gls_run_query: the run is still in progress            */
 } gls_status;
 
 /* Cell library (Sec. 2.1 "cells derived from basic gates"); pins a, b, c. */
@@ -186,6 +187,10 @@ int gls_simulate_batch(gls_ctx *ctx, int32_t n_items, const int32_t *netlist_ids
 /* Enqueue the same run again (same buffers, current stimulus contents). */
 int gls_rerun(gls_ctx *ctx, int32_t run_id, void *cuda_stream);
 
+/* Non-blocking: GLS_OK when the run's last enqueued evaluation has finished,
+   GLS_EAGAIN while it is still in progress. */
+int gls_run_query(gls_ctx *ctx, int32_t run_id);
+
 /*
  * Wait for a run and report it: *total_events = output transitions of all
  * gates, *kernel_ms = device time of the last enqueued evaluation (CUDA
@@ -198,6 +203,12 @@ int gls_rerun(gls_ctx *ctx, int32_t run_id, void *cuda_stream);
  * gate gave up (dependency schedule).
  */
 int gls_run_stats(gls_ctx *ctx, int32_t run_id, int64_t *total_events, double *kernel_ms);
+
+/* Wait for a run and report its event arena: *arena_demand = words the gates
+   reserved (Eq. 2 bounds, padded to 128-byte lines), *arena_capacity = the
+   run's arena size; either pointer may be NULL.  The demand sizes later runs
+   of similar inputs (the serving admission model). */
+int gls_run_info(gls_ctx *ctx, int32_t run_id, int64_t *arena_demand, int64_t *arena_capacity);
 
 /*
  * Copy one net's waveform to the host (item 0 of a batch): times into
@@ -225,8 +236,13 @@ typedef enum gls_option {
                                        position never signals completion, so its readers wait out
                                        the limit and the run reports GLS_ETIMEOUT (-1 = off)     */
     GLS_OPT_KERNEL = 5,         /* GLS_KERNEL_WINDOWED (default) or GLS_KERNEL_SEGMENTED        */
-    GLS_OPT_SEGMENT = 6         /* segmented kernel: input transitions per lane segment, >= 1
+    GLS_OPT_SEGMENT = 6,        /* segmented kernel: input transitions per lane segment, >= 1
                                    (default 32); a gate uses min(32, ceil(inputs / this)) lanes */
+    GLS_OPT_POOL_BYTES = 7      /* > 0: allocate one device region of this size now and carve
+                                   every later netlist, stimulus and run buffer from it (first
+                                   fit, no cudaMalloc/cudaFree per run, so creating and freeing
+                                   runs does not synchronise the device); 0: free the pool.
+                                   Only when no pool block is in use. */
 } gls_option;
 
 /* Gate kernel variants; all compute the same waveforms.

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -274,15 +275,64 @@ struct gls_ctx {
     std::unordered_map<int32_t, std::unique_ptr<NetlistObj>> netlists;
     std::unordered_map<int32_t, std::unique_ptr<StimObj>> stims;
     std::unordered_map<int32_t, std::unique_ptr<RunObj>> runs;
-    std::unordered_map<void *, size_t> allocs;
+    std::unordered_map<void *, size_t> allocs;       // cudaMalloc'd blocks
+    // optional device pool: one region carved first-fit into 256-byte aligned blocks
+    char *pool = nullptr;
+    uint64_t pool_bytes = 0;
+    std::map<uint64_t, uint64_t> pool_free;           // offset -> size of free ranges
+    std::unordered_map<void *, uint64_t> pool_allocs; // block -> size
     uint32_t *d_status = nullptr;       // scratch for stimulus packing (3 words)
 };
 
 namespace {
 
+// First-fit allocation from the context's pool (no CUDA call, so creating
+// and freeing run buffers never synchronises the device).
+void *pool_take(gls_ctx *c, uint64_t bytes) {
+    bytes = (bytes + 255) & ~255ull;
+    for (auto it = c->pool_free.begin(); it != c->pool_free.end(); ++it) {
+        if (it->second < bytes) continue;
+        const uint64_t off = it->first, size = it->second;
+        c->pool_free.erase(it);
+        if (size > bytes) c->pool_free[off + bytes] = size - bytes;
+        void *p = c->pool + off;
+        c->pool_allocs[p] = bytes;
+        return p;
+    }
+    return nullptr;
+}
+
+bool pool_give(gls_ctx *c, void *p) {
+    auto a = c->pool_allocs.find(p);
+    if (a == c->pool_allocs.end()) return false;
+    uint64_t off = (uint64_t)((char *)p - c->pool), size = a->second;
+    c->pool_allocs.erase(a);
+    auto next = c->pool_free.lower_bound(off);
+    if (next != c->pool_free.end() && next->first == off + size) {   // merge with the following range
+        size += next->second;
+        next = c->pool_free.erase(next);
+    }
+    if (next != c->pool_free.begin()) {                               // and with the preceding one
+        auto prev = std::prev(next);
+        if (prev->first + prev->second == off) {
+            prev->second += size;
+            return true;
+        }
+    }
+    c->pool_free[off] = size;
+    return true;
+}
+
 int dalloc(gls_ctx *c, void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (c->pool) {
+        *p = pool_take(c, bytes);
+        if (!*p)
+            return fail(GLS_ENOMEM, "device pool of %llu bytes has no free block of %llu bytes",
+                        (unsigned long long)c->pool_bytes, (unsigned long long)bytes);
+        return GLS_OK;
+    }
     if (c->used + bytes > c->budget)
         return fail(GLS_ENOMEM, "device budget exceeded (%llu + %llu > %llu bytes)", (unsigned long long)c->used,
                     (unsigned long long)bytes, (unsigned long long)c->budget);
@@ -307,6 +357,7 @@ int dalloc_n(gls_ctx *c, T **p, size_t n) {
 
 void dfree(gls_ctx *c, void *p) {
     if (!p) return;
+    if (pool_give(c, p)) return;
     auto it = c->allocs.find(p);
     if (it != c->allocs.end()) {
         c->used -= it->second;
@@ -513,6 +564,10 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
         // default: 256 words per stimulus transition plus 1 Mi, at most half
         // of what is left of the budget (GLS_EOVERFLOW reports the demand)
         uint64_t left = c->budget > c->used ? c->budget - c->used : 0;
+        if (c->pool) {
+            left = 0;
+            for (auto &kv : c->pool_free) left = std::max(left, kv.second);
+        }
         uint64_t meta = (uint64_t)r->n_nets * 16 + (uint64_t)r->depth * 4 + 4096;
         uint64_t cap = left > meta ? (left - meta) / 2 / 4 : 0;
         uint64_t want = 256ull * (uint64_t)stim_events + (1ull << 20);
@@ -697,6 +752,7 @@ void gls_destroy(gls_ctx *c) {
     for (auto &kv : c->stims) free_stim(c, kv.second.get());
     for (auto &kv : c->netlists) free_netlist(c, kv.second.get());
     dfree(c, c->d_status);
+    if (c->pool) cudaFree(c->pool);
     cudaStreamDestroy(c->stream);
     cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -832,6 +888,30 @@ int gls_rerun(gls_ctx *c, int32_t run_id, void *cuda_stream) {
     return GLS_OK;
 }
 
+int gls_run_query(gls_ctx *c, int32_t run_id) {
+    if (!c) return fail(GLS_EINVAL, "NULL context");
+    RunObj *r = find_run(c, run_id);
+    if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    CK(cudaSetDevice(c->device));
+    const cudaError_t e = cudaEventQuery(r->ev1);
+    if (e == cudaSuccess) return GLS_OK;
+    if (e == cudaErrorNotReady) return GLS_EAGAIN;
+    return fail(GLS_ECUDA, "cudaEventQuery: %s", cudaGetErrorString(e));
+}
+
+int gls_run_info(gls_ctx *c, int32_t run_id, int64_t *arena_demand, int64_t *arena_capacity) {
+    if (!c) return fail(GLS_EINVAL, "NULL context");
+    RunObj *r = find_run(c, run_id);
+    if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    CK(cudaSetDevice(c->device));
+    CK(cudaEventSynchronize(r->ev1));
+    unsigned long long top = 0;
+    CK(cudaMemcpy(&top, r->dev.arena_top, sizeof top, cudaMemcpyDeviceToHost));
+    if (arena_demand) *arena_demand = (int64_t)top;
+    if (arena_capacity) *arena_capacity = (int64_t)r->dev.arena_cap;
+    return GLS_OK;
+}
+
 int gls_run_stats(gls_ctx *c, int32_t run_id, int64_t *total_events, double *kernel_ms) {
     if (!c) return fail(GLS_EINVAL, "NULL context");
     RunObj *r = find_run(c, run_id);
@@ -939,6 +1019,32 @@ int gls_set_option(gls_ctx *c, int option, int64_t value) {
         if (value < 1 || value > (1 << 20)) return fail(GLS_EINVAL, "segment target must be in [1, 2^20]");
         c->seg_target = (uint32_t)value;
         return GLS_OK;
+    case GLS_OPT_POOL_BYTES: {
+        if (value < 0) return fail(GLS_EINVAL, "pool size must be >= 0");
+        if (!c->pool_allocs.empty()) return fail(GLS_EINVAL, "the pool still holds %zu blocks", c->pool_allocs.size());
+        if (c->pool) {
+            CK(cudaFree(c->pool));
+            c->used -= c->pool_bytes;
+            c->pool = nullptr;
+            c->pool_bytes = 0;
+            c->pool_free.clear();
+        }
+        if (value == 0) return GLS_OK;
+        const uint64_t bytes = ((uint64_t)value + 255) & ~255ull;
+        if (c->used + bytes > c->budget)
+            return fail(GLS_ENOMEM, "pool of %llu bytes exceeds the device budget", (unsigned long long)bytes);
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GLS_ENOMEM, "cudaMalloc(pool %llu): %s", (unsigned long long)bytes, cudaGetErrorString(e));
+        }
+        c->pool = static_cast<char *>(p);
+        c->pool_bytes = bytes;
+        c->used += bytes;
+        c->pool_free[0] = bytes;
+        return GLS_OK;
+    }
     case GLS_OPT_TEST_WITHHOLD_GATE:
         if (value < -1 || value > INT32_MAX) return fail(GLS_EINVAL, "gate index out of range");
         c->withhold_gate = (int32_t)value;

@@ -17,10 +17,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgls.so")
 
-GLS_OK, GLS_EINVAL, GLS_ECYCLE, GLS_ESTIM, GLS_ERANGE, GLS_ENOMEM, GLS_EOVERFLOW, GLS_ETIMEOUT, GLS_ECUDA = \
-    0, -1, -2, -3, -4, -5, -6, -7, -8
+GLS_OK, GLS_EINVAL, GLS_ECYCLE, GLS_ESTIM, GLS_ERANGE, GLS_ENOMEM, GLS_EOVERFLOW, GLS_ETIMEOUT, GLS_ECUDA, \
+    GLS_EAGAIN = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 STATUS_NAMES = {0: "GLS_OK", -1: "GLS_EINVAL", -2: "GLS_ECYCLE", -3: "GLS_ESTIM", -4: "GLS_ERANGE",
-                -5: "GLS_ENOMEM", -6: "GLS_EOVERFLOW", -7: "GLS_ETIMEOUT", -8: "GLS_ECUDA"}
+                -5: "GLS_ENOMEM", -6: "GLS_EOVERFLOW", -7: "GLS_ETIMEOUT", -8: "GLS_ECUDA", -9: "GLS_EAGAIN"}
 CELLS = ["INV", "BUF", "AND2", "OR2", "NAND2", "NOR2", "XOR2", "XNOR2", "MUX2", "AOI21", "OAI21"]
 GLS_MAX_DELAY_SPREAD = 255
 GLS_NOALLOC_MAX_LEVELS = 4000
@@ -43,6 +43,8 @@ SIGNATURES = [
     ("gls_simulate", ctypes.c_int, [P, i32, i32, i64, P, ctypes.POINTER(i32)]),
     ("gls_simulate_batch", ctypes.c_int, [P, i32, P, P, P, i64, P, ctypes.POINTER(i32)]),
     ("gls_rerun", ctypes.c_int, [P, i32, P]),
+    ("gls_run_query", ctypes.c_int, [P, i32]),
+    ("gls_run_info", ctypes.c_int, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     ("gls_run_stats", ctypes.c_int, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]),
     ("gls_read_waveform", ctypes.c_int, [P, i32, i32, P, P, i64, ctypes.POINTER(i64)]),
     ("gls_read_all", ctypes.c_int, [P, i32, P, P, i64]),
@@ -51,7 +53,8 @@ SIGNATURES = [
     ("gls_simulate_noalloc", ctypes.c_int, [P, i32, i32, P, P, P, i64, P, P]),
     ("gls_release", ctypes.c_int, [P, i32]),
 ]
-GLS_OPT_SCHEDULE, GLS_OPT_WARPS_PER_CTA, GLS_OPT_WAIT_LIMIT_MS, GLS_OPT_TEST_WITHHOLD_GATE, GLS_OPT_KERNEL, GLS_OPT_SEGMENT = 1, 2, 3, 4, 5, 6
+GLS_OPT_SCHEDULE, GLS_OPT_WARPS_PER_CTA, GLS_OPT_WAIT_LIMIT_MS, GLS_OPT_TEST_WITHHOLD_GATE, GLS_OPT_KERNEL, GLS_OPT_SEGMENT, \
+    GLS_OPT_POOL_BYTES = 1, 2, 3, 4, 5, 6, 7
 GLS_KERNEL_SEGMENTED, GLS_KERNEL_WINDOWED, GLS_KERNEL_WINDOWED_WIDE = 0, 1, 2
 KERNELS = {"segmented": GLS_KERNEL_SEGMENTED, "windowed": GLS_KERNEL_WINDOWED, "wide": GLS_KERNEL_WINDOWED_WIDE}
 GLS_SCHEDULE_LEVELS, GLS_SCHEDULE_DEPENDENCY = 0, 1
@@ -238,6 +241,20 @@ class Context:
 
     def rerun(self, run_id: int, stream=None):
         self._ck(self.lib.gls_rerun(self.h, run_id, _stream_handle(stream)))
+
+    def run_done(self, run_id: int) -> bool:
+        """True once the run's last enqueued evaluation finished (does not block)."""
+        rc = self.lib.gls_run_query(self.h, run_id)
+        if rc == GLS_EAGAIN:
+            return False
+        self._ck(rc)
+        return True
+
+    def run_info(self, run_id: int):
+        """(arena demand, arena capacity) in 32-bit words."""
+        d, c = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._ck(self.lib.gls_run_info(self.h, run_id, ctypes.byref(d), ctypes.byref(c)))
+        return d.value, c.value
 
     def run_stats(self, run_id: int) -> RunStats:
         tot, ms = ctypes.c_int64(0), ctypes.c_double(0.0)

@@ -1,0 +1,243 @@
+"""Serving: continuous batching of simulation requests over resident netlists.
+
+A request names a resident netlist and a stimulus window t_limit (ps): it asks
+for the waveforms of that netlist under the first t_limit ps of the netlist's
+resident stimulus.  The dispatcher:
+  - admits waiting requests as soon as a stream slot and enough of the HBM
+    budget are free, estimating each request's footprint from a per-netlist
+    calibration (event-arena words per stimulus transition, measured on one
+    full-window run);
+  - batches waiting requests of the same netlist into one launch
+    (gls_simulate_batch with per-item time limits; the netlist's gate records
+    are shared, not copied) -- requests that arrive while others run are
+    admitted into new launches on other streams, so their work overlaps;
+  - retires finished launches with a non-blocking query, records each
+    request's latency (arrival -> results resident on the device) and
+    re-admits a launch whose arena was too small with the measured demand.
+Device buffers come from the context's pool, so admitting and retiring never
+synchronises the device.  batching=False, streams=1 gives the plain form:
+one request per launch, one launch at a time, in arrival order.
+"""
+from __future__ import annotations
+
+import threading
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import gls as _g
+from .gls import Context, GlsError
+
+
+@dataclass
+class Request:
+    rid: int
+    netlist: str       # key of a resident netlist
+    t_limit: int       # window: stimulus transitions before this time (ps)
+    arrival: float     # seconds after the start of the trace
+    t_done: float = -1.0
+    out_transitions: int = 0
+    attempts: int = 0
+    result: tuple | None = None   # (off, packed) when the server keeps results
+
+
+@dataclass
+class Resident:
+    key: str
+    nid: int
+    sid: int
+    n_nets: int
+    pi_events: int
+    window: int
+    words_per_event: float = 0.0
+
+
+@dataclass
+class ServeStats:
+    requests: int
+    wall_s: float
+    p50_ms: float
+    p99_ms: float
+    mean_ms: float
+    transitions: int
+    transitions_per_s: float
+    launches: int
+    mean_batch: float
+    readmitted: int
+    latencies_ms: list = field(default_factory=list)
+
+
+class Server:
+    def __init__(self, ctx: Context, budget_bytes: int, max_batch: int = 16, streams: int = 4,
+                 batching: bool = True, safety: float = 1.3, keep_results: bool = False):
+        import torch
+        self.ctx = ctx
+        self.budget = int(budget_bytes)
+        self.max_batch = max_batch if batching else 1
+        self.safety = safety
+        self.keep = keep_results
+        self.streams = [torch.cuda.Stream() for _ in range(max(1, streams))]
+        self.res: dict[str, Resident] = {}
+
+    # ---- resident netlists ----
+    def add_resident(self, key: str, netlist, stimulus, window: int):
+        nid = self.ctx.load_netlist(netlist)
+        sid = self.ctx.load_stimulus(stimulus, n_pi=netlist.n_pi)
+        self.res[key] = Resident(key, nid, sid, int(netlist.n_pi + netlist.n_gates), int(stimulus.n_events),
+                                 int(window))
+
+    def calibrate(self):
+        """Event-arena words per stimulus transition of each resident netlist,
+        from one full-window run (the footprint model of admission)."""
+        for r in self.res.values():
+            arena = 0
+            while True:
+                rid = self.ctx.simulate(r.nid, r.sid, arena_events=arena)
+                rc, demand, _ = self.ctx.run_stats_raw(rid)
+                if rc == 0:
+                    demand = self.ctx.run_info(rid)[0]
+                self.ctx.release(rid)
+                if rc == 0:
+                    break
+                if rc != _g.GLS_EOVERFLOW:
+                    raise GlsError(rc, "calibration run failed")
+                arena = int(demand * 1.5) + 4096
+            r.words_per_event = max(1.0, demand / max(1, r.pi_events))
+
+    def estimate_words(self, key: str, t_limit: int) -> int:
+        r = self.res[key]
+        frac = min(1.0, max(t_limit, 1) / r.window)
+        return int(r.words_per_event * r.pi_events * frac * self.safety) + 4096
+
+    def _footprint(self, words: int, n_items: int, n_nets: int) -> int:
+        return 4 * words + n_items * n_nets * 16 + (1 << 20)
+
+    # ---- serving ----
+    def serve(self, requests: list[Request]) -> ServeStats:
+        ctx = self.ctx
+        pending: deque[Request] = deque()
+        lock = threading.Lock()
+        t0 = time.perf_counter() + 0.05
+        done_arriving = threading.Event()
+
+        def arrivals():
+            for q in sorted(requests, key=lambda x: x.arrival):
+                dt = t0 + q.arrival - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                with lock:
+                    pending.append(q)
+            done_arriving.set()
+
+        th = threading.Thread(target=arrivals, daemon=True)
+        th.start()
+        inflight = []            # (run_id, reqs, stream index, bytes, words)
+        free_streams = list(range(len(self.streams)))
+        used = 0
+        launches, items, readmitted = 0, 0, 0
+        scale: dict[str, float] = {}
+        while True:
+            progressed = False
+            # retire finished launches
+            for entry in list(inflight):
+                rid, reqs, si, nbytes, words = entry
+                if not ctx.run_done(rid):
+                    continue
+                rc, total, _ = ctx.run_stats_raw(rid)
+                now = time.perf_counter()
+                if rc == _g.GLS_EOVERFLOW:
+                    # the estimate was too small: grow this netlist's model and re-admit
+                    key = reqs[0].netlist
+                    scale[key] = scale.get(key, 1.0) * max(2.0, 1.2 * total / max(1, words))
+                    with lock:
+                        for q in reversed(reqs):
+                            q.attempts += 1
+                            pending.appendleft(q)
+                    readmitted += len(reqs)
+                elif rc != 0:
+                    raise GlsError(rc, ctx.lib.gls_last_error(ctx.h).decode())
+                else:
+                    # the launch's gate transitions, shared among its requests
+                    share, rem = divmod(total, len(reqs))
+                    for i, q in enumerate(reqs):
+                        q.t_done = now - t0
+                        q.out_transitions = share + (rem if i == 0 else 0)
+                        if self.keep:
+                            q.result = ctx.read_item(rid, i)
+                ctx.release(rid)
+                inflight.remove(entry)
+                free_streams.append(si)
+                used -= nbytes
+                progressed = True
+            # admit waiting requests
+            while free_streams:
+                with lock:
+                    if not pending:
+                        break
+                    head = pending[0]
+                    group = [head]
+                    if self.max_batch > 1:
+                        for q in list(pending)[1:]:
+                            if len(group) >= self.max_batch:
+                                break
+                            if q.netlist == head.netlist:
+                                group.append(q)
+                r = self.res[head.netlist]
+                sc = scale.get(head.netlist, 1.0)
+                words = [int(self.estimate_words(q.netlist, q.t_limit) * sc) for q in group]
+                while len(group) > 1 and used + self._footprint(sum(words), len(group), r.n_nets) > self.budget:
+                    group.pop()
+                    words.pop()
+                need = self._footprint(sum(words), len(group), r.n_nets)
+                if used + need > self.budget and inflight:
+                    break       # wait for memory
+                si = free_streams.pop()
+                with lock:
+                    for q in group:
+                        pending.remove(q)
+                try:
+                    rid = ctx.simulate_batch([r.nid] * len(group), [r.sid] * len(group),
+                                             t_limits=[q.t_limit for q in group], arena_events=sum(words),
+                                             stream=self.streams[si])
+                except GlsError:
+                    free_streams.append(si)
+                    with lock:
+                        for q in reversed(group):
+                            pending.appendleft(q)
+                    if not inflight:
+                        raise
+                    break
+                inflight.append((rid, group, si, need, sum(words)))
+                used += need
+                launches += 1
+                items += len(group)
+                progressed = True
+            with lock:
+                idle = not pending
+            if done_arriving.is_set() and idle and not inflight:
+                break
+            if not progressed:
+                time.sleep(50e-6)
+        th.join()
+        lat = np.array([(q.t_done - q.arrival) * 1000.0 for q in requests])
+        wall = max(q.t_done for q in requests) - min(q.arrival for q in requests)
+        tr = int(sum(q.out_transitions for q in requests))
+        return ServeStats(len(requests), wall, float(np.percentile(lat, 50)), float(np.percentile(lat, 99)),
+                          float(lat.mean()), tr, tr / max(wall, 1e-9), launches, items / max(1, launches),
+                          readmitted, lat.tolist())
+
+
+def poisson_trace(n_seconds: float, rate: float, keys: list[str], wmin: int, wmax: int, seed: int) -> list[Request]:
+    """Seeded request stream: Poisson arrivals, a uniformly chosen resident
+    netlist, a window log-uniform in [wmin, wmax] ps."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= n_seconds:
+            break
+        w = int(np.exp(rng.uniform(np.log(wmin), np.log(wmax))))
+        out.append(Request(len(out), keys[int(rng.integers(0, len(keys)))], w, t))
+    return out
