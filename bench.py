@@ -49,6 +49,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve"],
+                    help="plain: one 1M-gate run (the headline); batch: 64 stimulus sets + 16 netlists "
+                         "in batched launches vs one at a time; serve: 200 req/s over resident netlists, "
+                         "continuous batching vs plain")
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--batch-sets", type=int, default=64)
+    ap.add_argument("--batch-netlists", type=int, default=16)
     ap.add_argument("--workload", default="ind1m")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-frac", type=float, default=0.005,
@@ -374,10 +382,174 @@ def run_own(a):
     return 0
 
 
+def scaled_recipe(gates: int, seed: int):
+    """A netlist of the 1M-gate recipe's distributions at another size:
+    PIs = gates / 50, depth 20 log10(gates) - 60 clamped to [8, 60]."""
+    import synth
+    r = synth.RECIPES["ind1m"]
+    depth = int(min(60, max(8, round(20 * np.log10(gates) - 60))))
+    net = dict(r["net"], n_gates=int(gates), n_pi=max(16, int(gates) // 50), depth=depth)
+    return net, dict(r["stim"]), seed
+
+
+def make_scaled(gates: int, seed: int):
+    import synth
+    net, stim, seed = scaled_recipe(gates, seed)
+    nl = synth.make_netlist(seed=seed, **net)
+    st = synth.make_stimulus(net["n_pi"], seed=seed + 1000003, **stim)
+    return nl, st, net, stim
+
+
+def run_batch(a):
+    """Batched form: 64 seeded stimulus sets on the 1M-gate netlist plus 16
+    netlists of log-uniform size (10k-2M gates) with their own stimuli.
+    Items run in batched launches (waves sized to fit HBM; the kernel
+    configuration chosen by the autotuner) and, for comparison, one at a time."""
+    import torch
+    import paper_2304_13398_gb300 as gls
+    import synth
+    from paper_2304_13398_gb300.autotune import autotune
+    torch.cuda.set_device(0)
+    ctx = gls.Context(0)
+    r = synth.RECIPES["ind1m"]
+    nl = synth.make_netlist(seed=a.seed, **r["net"])
+    nid = ctx.load_netlist(nl)
+    sids, pi_events = [], []
+    for s in range(1, a.batch_sets + 1):
+        st = synth.make_stimulus(nl.n_pi, seed=s, **r["stim"])
+        sids.append(ctx.load_stimulus(st))
+        pi_events.append(st.n_events)
+    rng = np.random.default_rng(a.seed + 77)
+    sizes = np.exp(rng.uniform(np.log(1e4), np.log(2e6), a.batch_netlists)).astype(int)
+    mixed = []
+    for i, G in enumerate(sizes):
+        mnl, mst, _, _ = make_scaled(int(G), 5000 + i)
+        mixed.append((ctx.load_netlist(mnl), ctx.load_stimulus(mst), int(G), mst.n_events))
+    # per-replica arena demand, from one plain run
+    rid = ctx.simulate(nid, sids[0])
+    ctx.run_stats(rid)
+    demand = ctx.run_info(rid)[0]
+    ctx.release(rid)
+    free, _ = torch.cuda.mem_get_info()
+    per = int(demand * 1.05) + (1 << 20)
+    wave = max(1, min(a.batch_sets, int(0.8 * free / (4 * per + 16 * (nl.n_pi + nl.n_gates)))))
+    # autotune on one wave of replicas
+    tune = autotune(ctx, lambda: ctx.simulate_batch([nid] * wave, sids[:wave], arena_events=per * wave))
+    waves, b_ms, b_tr, b_wall = [], 0.0, 0, 0.0
+    totals = {}
+    for w0 in range(0, a.batch_sets, wave):
+        ids = sids[w0:w0 + wave]
+        t0 = time.perf_counter()
+        rid = ctx.simulate_batch([nid] * len(ids), ids, arena_events=per * len(ids))
+        st = ctx.run_stats(rid)
+        b_wall += time.perf_counter() - t0
+        b_ms += st.kernel_ms
+        b_tr += st.total_events
+        waves.append({"items": len(ids), "kernel_ms": st.kernel_ms, "transitions": st.total_events})
+        ctx.release(rid)
+    # the 16 distinct netlists together (one launch, records interleaved by level)
+    mids = [m[0] for m in mixed]
+    msids = [m[1] for m in mixed]
+    rid = ctx.simulate_batch(mids, msids)
+    rc, tot, ms = ctx.run_stats_raw(rid)
+    while rc == gls.gls.GLS_EOVERFLOW:
+        ctx.release(rid)
+        rid = ctx.simulate_batch(mids, msids, arena_events=int(tot * 1.25) + (1 << 20))
+        rc, tot, ms = ctx.run_stats_raw(rid)
+    ctx.release(rid)
+    b_ms += ms
+    b_tr += tot
+    waves.append({"items": len(mids), "kernel_ms": ms, "transitions": tot, "netlists": [int(x) for x in sizes]})
+    # plain: every item alone, same configuration
+    p_ms, p_tr = 0.0, 0
+    rid = ctx.simulate(nid, sids[0], arena_events=per)
+    ctx.run_stats(rid)
+    ctx.release(rid)
+    for sid in sids:
+        rid = ctx.simulate(nid, sid, arena_events=per)
+        st = ctx.run_stats(rid)
+        p_ms += st.kernel_ms
+        p_tr += st.total_events
+        ctx.release(rid)
+    for m_nid, m_sid, _, _ in mixed:
+        rid = ctx.simulate(m_nid, m_sid)
+        rc, tot, ms = ctx.run_stats_raw(rid)
+        while rc == gls.gls.GLS_EOVERFLOW:
+            ctx.release(rid)
+            rid = ctx.simulate(m_nid, m_sid, arena_events=int(tot * 1.25) + (1 << 20))
+            rc, tot, ms = ctx.run_stats_raw(rid)
+        p_ms += ms
+        p_tr += tot
+        ctx.release(rid)
+    ctx.close()
+    line = {"metric": "batched output transitions/s (64 stimulus sets x 1M gates + 16 netlists 10k-2M gates)",
+            "value": b_tr / (b_ms / 1000.0), "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "mode": "batch", "transitions": b_tr, "device_ms": b_ms, "wall_s": b_wall,
+            "plain": {"value": p_tr / (p_ms / 1000.0), "unit": UNIT, "device_ms": p_ms, "transitions": p_tr},
+            "speedup_vs_plain": (b_tr / b_ms) / (p_tr / p_ms), "items_match_plain": b_tr == p_tr,
+            "wave_size": wave, "waves": waves, "autotune": {"best": tune.best,
+                                                             "trials": [[c, m] for c, m in tune.timings_ms]},
+            "data": "synthetic", "dtype": "u32 packed events"}
+    print(json.dumps(line))
+    return 0
+
+
+def run_serve(a):
+    """Served form: a seeded Poisson request stream (200 req/s, 30 s) over 8
+    resident netlists of log-uniform size (5k-5M gates), stimulus windows
+    log-uniform in [1e4, 1e7] ps, 150 GB admission budget; continuous
+    batching against the plain one-request-at-a-time form on the same trace."""
+    import copy
+    import torch
+    import paper_2304_13398_gb300 as gls
+    from paper_2304_13398_gb300.serve import Server, poisson_trace
+    torch.cuda.set_device(0)
+    ctx = gls.Context(0)
+    free, _ = torch.cuda.mem_get_info()
+    ctx.set_option(gls.gls.GLS_OPT_POOL_BYTES, int(min(free * 0.85, 200e9)))
+    budget = int(150e9)
+    rng = np.random.default_rng(a.seed + 99)
+    sizes = np.exp(rng.uniform(np.log(5e3), np.log(5e6), 8)).astype(int)
+    res = []
+    for i, G in enumerate(sizes):
+        nl, st, _, stim = make_scaled(int(G), 7000 + i)
+        res.append((f"n{i}", nl, st, stim["window"]))
+    out = {}
+    for mode, kw in (("served", dict(batching=True, streams=4, max_batch=16)),
+                     ("plain", dict(batching=False, streams=1))):
+        srv = Server(ctx, budget_bytes=budget, **kw)
+        for key, nl, st, window in res:
+            srv.add_resident(key, nl, st, window)
+        srv.calibrate()
+        trace = poisson_trace(a.serve_seconds, a.serve_rate, [x[0] for x in res], 10_000, 10_000_000, a.seed)
+        t0 = time.perf_counter()
+        stt = srv.serve(trace)
+        out[mode] = {"requests": stt.requests, "p50_ms": stt.p50_ms, "p99_ms": stt.p99_ms, "mean_ms": stt.mean_ms,
+                     "transitions": stt.transitions, "transitions_per_s": stt.transitions_per_s,
+                     "launches": stt.launches, "mean_batch": stt.mean_batch, "readmitted": stt.readmitted,
+                     "wall_s": time.perf_counter() - t0}
+        for key, *_ in res:
+            ctx.release(srv.res[key].sid)
+            ctx.release(srv.res[key].nid)
+    ctx.close()
+    line = {"metric": "served output transitions/s and p50/p99 latency (200 req/s, 8 resident netlists 5k-5M gates)",
+            "value": out["served"]["transitions_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "mode": "serve", "served": out["served"], "plain": out["plain"],
+            "netlists": [int(x) for x in sizes], "budget_bytes": budget,
+            "latency": "request arrival -> its waveforms resident on the device",
+            "data": "synthetic", "dtype": "u32 packed events"}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.mode == "batch":
+        return run_batch(a)
+    if a.mode == "serve":
+        return run_serve(a)
     return run_own(a)
 
 

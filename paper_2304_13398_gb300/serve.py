@@ -88,13 +88,15 @@ class Server:
         self.res[key] = Resident(key, nid, sid, int(netlist.n_pi + netlist.n_gates), int(stimulus.n_events),
                                  int(window))
 
-    def calibrate(self):
+    def calibrate(self, frac: float = 0.2):
         """Event-arena words per stimulus transition of each resident netlist,
-        from one full-window run (the footprint model of admission)."""
+        from one run over the first `frac` of its window (the footprint model
+        of admission; transitions are spread evenly over the window)."""
         for r in self.res.values():
+            t_limit = max(1, int(r.window * frac))
             arena = 0
             while True:
-                rid = self.ctx.simulate(r.nid, r.sid, arena_events=arena)
+                rid = self.ctx.simulate_batch([r.nid], [r.sid], t_limits=[t_limit], arena_events=arena)
                 rc, demand, _ = self.ctx.run_stats_raw(rid)
                 if rc == 0:
                     demand = self.ctx.run_info(rid)[0]
@@ -104,7 +106,7 @@ class Server:
                 if rc != _g.GLS_EOVERFLOW:
                     raise GlsError(rc, "calibration run failed")
                 arena = int(demand * 1.5) + 4096
-            r.words_per_event = max(1.0, demand / max(1, r.pi_events))
+            r.words_per_event = max(1.0, demand / max(1.0, r.pi_events * frac))
 
     def estimate_words(self, key: str, t_limit: int) -> int:
         r = self.res[key]
