@@ -61,7 +61,7 @@ struct __align__(16) WarpSmem {
     static constexpr int WIN = CH + 8;     // aligned lead (<= 3) + CH + sentinel, multiple of 4
     uint32_t win[2][3][WIN];  // double-buffered pin windows
     uint32_t B[2 * CH + 4];   // pins a+b merged (3-input cells), sentinel-terminated
-    uint16_t Binfo[2 * CH];   // source of B[i]: pin b flag (bit 15) | index in its window
+    uint16_t Binfo[2 * CH + 8];   // source of B[i]: pin b flag (bit 15) | index in its window (+ read pad)
     uint32_t cand[3 * CH];    // per-lane stacks of scheduled transitions (t_r << 2 | v)
     uint32_t Q[PCAP + 3 * CH];  // carried transitions (front) + this chunk's survivors
 };
@@ -114,9 +114,23 @@ struct GateCtx {
     const uint32_t *src[3];
     uint32_t len[3];
     uint32_t rise[3], fall[3], dx[3];
-    uint32_t dmin;
+    uint32_t dmin, dmax;
     uint64_t lut_lo, lut_hi;
+    // min over the pins of a pin set of (delay - dmin), one byte per set
+    // (bit p = pin p; byte 0, the empty set, is 0): sets 0-3 in *_lo,
+    // 4-7 in *_hi; for a fall (f), a rise (r) and a change to X (x)
+    uint32_t df_lo, df_hi, dr_lo, dr_hi, dx_lo, dx_hi;
 };
+
+// Delay of a timestamp at which the pins of set `grp` changed and the cell's
+// value became F (min over those pins, Sec. 3 delay rule).  Byte grp of the
+// table pair; the other bytes of the permute read byte 0, which is 0.
+template <int K>
+__device__ __forceinline__ uint32_t group_delay(const GateCtx &g, uint32_t F, uint32_t grp) {
+    const uint32_t lo = F == 1u ? g.dr_lo : (F == 0u ? g.df_lo : g.dx_lo);
+    const uint32_t hi = K == 3 ? (F == 1u ? g.dr_hi : (F == 0u ? g.df_hi : g.dx_hi)) : 0u;
+    return g.dmin + __byte_perm(lo, hi, grp);
+}
 
 __device__ __forceinline__ uint32_t pin_delay(const GateCtx &g, int p, uint32_t F) {
     return F == 1u ? g.rise[p] : (F == 0u ? g.fall[p] : g.dx[p]);
@@ -248,6 +262,21 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
     g.dmin = (uint32_t)gr.dmin;
     g.lut_lo = c_lut[gr.type][0];
     g.lut_hi = c_lut[gr.type][1];
+    g.dmax = 0;
+    g.df_lo = g.df_hi = g.dr_lo = g.dr_hi = 0;
+#pragma unroll
+    for (int set = 1; set < 8; set++) {
+        uint32_t f = 255u, rr = 255u;   // sets with a pin >= K never occur
+#pragma unroll
+        for (int p = 0; p < K; p++)
+            if ((set >> p) & 1) { f = min(f, g.fall[p] - g.dmin); rr = min(rr, g.rise[p] - g.dmin); }
+        if (set < 4) { g.df_lo |= f << (8 * set); g.dr_lo |= rr << (8 * set); }
+        else { g.df_hi |= f << (8 * (set - 4)); g.dr_hi |= rr << (8 * (set - 4)); }
+    }
+    g.dx_lo = __vminu4(g.df_lo, g.dr_lo);
+    g.dx_hi = __vminu4(g.df_hi, g.dr_hi);
+#pragma unroll
+    for (int p = 0; p < K; p++) g.dmax = max(g.dmax, max(g.rise[p], g.fall[p]));
     const uint32_t out_net = gr.out_net;
 
     if (bound == 0) {   // no input transition: the output stays X (Algorithm 2 starts at X)
@@ -294,15 +323,32 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
             if (n[p] > 0 && cur[p] + (uint32_t)n[p] < g.len[p]) Tend = min(Tend, A[p][n[p] - 1] >> 2);
         const bool last = (Tend == kTimeInf);
         int m[3] = {0, 0, 0};
+        if (last) {
 #pragma unroll
-        for (int p = 0; p < K; p++) {
-            if (last) { m[p] = n[p]; continue; }
-            int c = 0;
-            for (int x0 = 0; x0 < n[p]; x0 += 32) {
-                const int x = x0 + lane;
-                c += __popc(__ballot_sync(FULL, x < n[p] && (A[p][x] >> 2) <= Tend));
+            for (int p = 0; p < K; p++) m[p] = n[p];
+        } else {
+            // m[p] = transitions of window p at or before Tend (a prefix):
+            // count the S-blocks whose last transition qualifies, then the
+            // qualifying transitions of the first block that does not
+            constexpr int S = CH / 32;
+            int q[3];
+#pragma unroll
+            for (int p = 0; p < K; p++) {
+                const int x = S * lane + S - 1;
+                q[p] = __popc(__ballot_sync(FULL, x < n[p] && (A[p][x] >> 2) <= Tend));
             }
-            m[p] = c;
+#pragma unroll
+            for (int p = 0; p < K; p++) {
+                const int x = S * q[p] + lane;
+                m[p] = S * q[p] + __popc(__ballot_sync(FULL, lane < S && x < n[p] && (A[p][x] >> 2) <= Tend));
+            }
+        }
+        if (lane == 0) {   // every t_r of this chunk is below the latest input time + dmax
+            uint32_t tmx = 0;
+#pragma unroll
+            for (int p = 0; p < K; p++)
+                if (m[p] > 0) tmx = max(tmx, A[p][m[p] - 1] >> 2);
+            if (tmx + g.dmax >= kTimeLimit) atomicOr(r.status, kStTimeRange);
         }
         // start the copies of the next chunk before evaluating this one
         uint32_t ncur[3] = {cur[0], cur[1], cur[2]};
@@ -339,24 +385,31 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         const int M = nL + nR;
         const int d0 = (lane * M) >> 5, d1 = ((lane + 1) * M) >> 5;
         int top = d0;
-        uint32_t trmax = 0;
+        // The walks are branch-free apart from the Eq. 1 pop loop: state
+        // updates are selects, the stack top sits in a register, and a
+        // candidate is always written one slot above the stack top (scratch
+        // inside the lane's share) and kept by advancing the top.
         if (K == 1) {
             // one pin: every transition is its own timestamp
             uint32_t Fprev = (lut1 >> (2 * (d0 > 0 ? (L[d0 - 1] & 3u) : (carry & 3u)))) & 3u;
+            uint32_t topv = 0;   // cand[top - 1] when top > d0
             for (int s = d0; s < d1; s++) {
                 const uint32_t e = L[s], t = e >> 2;
                 const uint32_t F = (lut1 >> (2 * (e & 3u))) & 3u;
-                if (F != Fprev) {
-                    const uint32_t tr = t + pin_delay(g, 0, F);
-                    trmax = max(trmax, tr);
-                    const uint32_t key = tr << 2;
-                    while (top > d0 && sm.cand[top - 1] >= key) top--;
-                    sm.cand[top++] = key | F;
+                const bool chg = F != Fprev;
+                const uint32_t key = (t + pin_delay(g, 0, F)) << 2;
+                while (chg && top > d0 && topv >= key) {
+                    top--;
+                    topv = top > d0 ? sm.cand[top - 1] : 0u;
                 }
+                sm.cand[top] = key | F;
+                top += chg;
+                topv = chg ? (key | F) : topv;
                 Fprev = F;
             }
         } else {
-            int i = corank(d0, L, nL, R, nR), j = d0 - i;
+            int i = corank(d0, L, nL, R, nR);
+            const int j = d0 - i;
             int c0, c1, c2;   // transitions of pins a, b, c consumed before d0
             if (K == 3) {
                 if (i == 0) { c0 = 0; c1 = 0; }
@@ -368,65 +421,64 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
                 c2 = j;
             } else { c0 = i; c1 = j; c2 = 0; }
             const int cc[3] = {c0, c1, c2};
-            uint32_t st = carry, lt[3] = {kTimeInf, kTimeInf, kTimeInf};
+            uint32_t st = carry;
+            uint32_t ltp[3] = {kTimeInf, kTimeInf, kTimeInf};
 #pragma unroll
             for (int p = 0; p < K; p++)
                 if (cc[p] > 0) {
                     const uint32_t e = A[p][cc[p] - 1];
                     st = setpin(st, p, e & 3u);
-                    lt[p] = e >> 2;
+                    ltp[p] = e >> 2;
                 }
             uint32_t hl = L[i], hr = R[j];
+            uint32_t hinfo = K == 3 ? sm.Binfo[i] : 0u;   // source of the L head (3-pin cells)
             uint32_t Fprev = 0;
+            uint32_t grp = 0;   // pins with a transition at the current timestamp
             if (d0 < d1) {
-                // cell value just before the first timestamp of this share
+                // cell value just before the first timestamp of this share, and
+                // the pins whose transitions at that timestamp precede the share
                 const uint32_t tf = min(hl, hr) >> 2;
                 uint32_t sb = st;
 #pragma unroll
                 for (int p = 0; p < K; p++)
-                    if (cc[p] > 0 && lt[p] == tf) {
+                    if (cc[p] > 0 && ltp[p] == tf) {
                         const uint32_t v = cc[p] >= 2 ? (A[p][cc[p] - 2] & 3u) : ((carry >> (2 * p)) & 3u);
                         sb = setpin(sb, p, v);
+                        grp |= 1u << p;
                     }
                 Fprev = K == 3 ? (uint32_t)(((sb & 32u) ? g.lut_hi : g.lut_lo) >> (2 * (sb & 31u))) & 3u
                                : (lut2 >> (2 * (sb & 15u))) & 3u;
             }
+            bool gend = false;   // the previous transition closed its timestamp
+            uint32_t topv = 0;   // cand[top - 1] when top > d0
             for (int s = d0; s < d1; s++) {
                 const bool tl = hl <= (hr | 3u);
                 const uint32_t e = tl ? hl : hr;
-                int pin;
-                if (tl) {
-                    pin = K == 3 ? (int)(sm.Binfo[i] >> 15) : 0;
-                    i++;
-                    hl = L[i];
-                } else {
-                    pin = K - 1;
-                    j++;
-                    hr = R[j];
-                }
+                const uint32_t pin = tl ? (K == 3 ? (hinfo >> 15) : 0u) : (uint32_t)(K - 1);
+                i += tl;   // s + 1 transitions consumed: i of L, s + 1 - i of R
+                const uint32_t y = tl ? L[i] : R[s + 1 - i];
+                hl = tl ? y : hl;
+                hr = tl ? hr : y;
+                if (K == 3) hinfo = sm.Binfo[i];
                 const uint32_t t = e >> 2;
-                st = setpin(st, pin, e & 3u);
-                lt[0] = pin == 0 ? t : lt[0];
-                lt[1] = pin == 1 ? t : lt[1];
-                if (K == 3) lt[2] = pin == 2 ? t : lt[2];
-                if ((min(hl, hr) >> 2) == t) continue;   // more transitions at this time
+                st = setpin(st, (int)pin, e & 3u);
+                grp = (gend ? 0u : grp) | (1u << pin);
+                const bool end = (min(hl, hr) >> 2) != t;   // last transition at this time
                 const uint32_t F = K == 3 ? (uint32_t)(((st & 32u) ? g.lut_hi : g.lut_lo) >> (2 * (st & 31u))) & 3u
                                           : (lut2 >> (2 * (st & 15u))) & 3u;
-                if (F != Fprev) {
-                    uint32_t d = kTimeInf;
-#pragma unroll
-                    for (int p = 0; p < K; p++)
-                        if (lt[p] == t) d = min(d, pin_delay(g, p, F));
-                    const uint32_t tr = t + d;
-                    trmax = max(trmax, tr);
-                    const uint32_t key = tr << 2;
-                    while (top > d0 && sm.cand[top - 1] >= key) top--;
-                    sm.cand[top++] = key | F;
+                const bool chg = end && F != Fprev;
+                const uint32_t key = (t + group_delay<K>(g, F, grp)) << 2;
+                while (chg && top > d0 && topv >= key) {
+                    top--;
+                    topv = top > d0 ? sm.cand[top - 1] : 0u;
                 }
-                Fprev = F;
+                sm.cand[top] = key | F;
+                top += chg;
+                topv = chg ? (key | F) : topv;
+                Fprev = end ? F : Fprev;
+                gend = end;
             }
         }
-        if (trmax >= kTimeLimit) atomicOr(r.status, kStTimeRange);
 
         // ---- 4./5. Eq. 1 across lanes, commit, carry ----
         const uint32_t Tfin = last ? kTimeInf : Tend + 1u + g.dmin;
@@ -809,7 +861,7 @@ __global__ void dependency_kernel(const GateRec *__restrict__ gates, int32_t n_g
         const GateRec gr = fetch_gate(gates, r, g, L);
         bool ok = true;
         if (lane < gr.k) {   // primary-input flags are set before the launch
-            const uint32_t *flag = r.done + gr.fin[lane];
+            const uint32_t *flag = r.done + (lane == 0 ? gr.fin[0] : (lane == 1 ? gr.fin[1] : gr.fin[2]));
             if (ld_acquire(flag) == 0u) {
                 const uint64_t t0 = globaltimer();
                 while (ld_acquire(flag) == 0u) {
