@@ -211,6 +211,25 @@ int gls_run_stats(gls_ctx *ctx, int32_t run_id, int64_t *total_events, double *k
 int gls_run_info(gls_ctx *ctx, int32_t run_id, int64_t *arena_demand, int64_t *arena_capacity);
 
 /*
+ * Plan the order in which the dependency schedule hands out the gates of a
+ * netlist (Algorithm 1: a gate runs once its fanin gates are done, so any
+ * topological order gives the same waveforms; the order only decides which
+ * ready work the device starts first).  Reads the per-net transition counts
+ * of item `item` of the finished run `run_id`, which must be an instance of
+ * `netlist_id` that completed without error; weighs each gate by 64 + the
+ * transitions on its fanin pins (its evaluation cost); and orders the gates
+ * by decreasing weighted longest path to a netlist output, critical path
+ * first.  A calibration run over a short window or another stimulus of the
+ * same design is enough: only the relative activity of the nets matters.
+ * Runs created afterwards with the dependency schedule on this netlist
+ * (alone or replicated in a batch) use the order; existing runs keep theirs.
+ * run_id = -1 restores level order.  Device memory: 48 bytes per gate.
+ * GLS_EINVAL for unknown ids or an item of another netlist; the run's own
+ * error when it failed.
+ */
+int gls_plan_order(gls_ctx *ctx, int32_t netlist_id, int32_t run_id, int32_t item);
+
+/*
  * Copy one net's waveform to the host (item 0 of a batch): times into
  * t[cap], values into v[cap].  *n_out always receives the length; GLS_EOVERFLOW if cap < length
  * (nothing copied).  Synchronises with the run.

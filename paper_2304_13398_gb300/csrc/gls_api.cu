@@ -217,6 +217,8 @@ struct NetlistObj {
     std::vector<int32_t> ext2int;      // host copy
     std::vector<GateRec> recs;         // host copy of the level-ordered records (batches)
     int32_t *d_level_begin = nullptr;  // [depth + 2] device copy of lv.level_begin (replicated items)
+    GateRec *d_plan = nullptr;         // records in the planned order (dependency schedule), or null
+    std::vector<GateRec *> plans;      // every planned copy, kept until the netlist is released
 };
 
 struct StimObj {
@@ -367,6 +369,7 @@ void dfree(gls_ctx *c, void *p) {
 }
 
 void free_netlist(gls_ctx *c, NetlistObj *n) {
+    for (GateRec *p : n->plans) dfree(c, p);
     dfree(c, n->d_gates);
     dfree(c, n->d_ext2int);
     dfree(c, n->d_level_begin);
@@ -536,6 +539,10 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
         r->dev.rep = n_items;
         r->dev.rep_nets = (int64_t)n->n_pi + n->n_gates;
         r->dev.lb = n->d_level_begin;
+        if (r->schedule == GLS_SCHEDULE_DEPENDENCY && n->d_plan) {
+            r->d_gates = n->d_plan;
+            r->dev.planned = 1;
+        }
     } else {      // records of all instances interleaved by level, net ids shifted
         std::vector<GateRec> comb((size_t)std::max(r->n_gates, 1));
         r->level_begin.assign(r->depth + 2, 0);
@@ -943,6 +950,61 @@ int gls_run_stats(gls_ctx *c, int32_t run_id, int64_t *total_events, double *ker
     if (status & kStTimeRange) return fail(GLS_ERANGE, "a computed time reached 2^30-1");
     if (status & kStTimeout) return fail(GLS_ETIMEOUT, "a wait for a fanin gate exceeded %.3f s",
                                          (double)r->dev.wait_limit_ns * 1e-9);
+    return GLS_OK;
+}
+
+// Critical-path-first order for the dependency schedule: w(g) = 64 + the
+// transitions on g's fanin pins in the calibration run, b(g) = w(g) + max b
+// over g's readers (longest weighted path to an output), gates by decreasing
+// b.  b of a fanin gate exceeds b of its reader (w >= 64), so the order is
+// topological, which keeps Algorithm 1's waits finite: every fanin gate of a
+// handed-out gate was handed out earlier.
+int gls_plan_order(gls_ctx *c, int32_t netlist_id, int32_t run_id, int32_t item) {
+    if (!c) return fail(GLS_EINVAL, "NULL context");
+    NetlistObj *n = find_netlist(c, netlist_id);
+    if (!n) return fail(GLS_EINVAL, "unknown netlist id %d", netlist_id);
+    CK(cudaSetDevice(c->device));
+    if (run_id == -1) {
+        n->d_plan = nullptr;
+        return GLS_OK;
+    }
+    RunObj *r = find_run(c, run_id);
+    if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    if (item < 0 || item >= (int32_t)r->items.size()) return fail(GLS_EINVAL, "item %d out of range", item);
+    if (r->items[item].netlist_id != netlist_id)
+        return fail(GLS_EINVAL, "item %d of run %d is not an instance of netlist %d", item, run_id, netlist_id);
+    int rc = gls_run_stats(c, run_id, nullptr, nullptr);
+    if (rc) return rc;
+    const int32_t P = n->n_pi, G = n->n_gates;
+    std::vector<uint32_t> len((size_t)P + G);
+    CK(cudaMemcpy(len.data(), r->dev.net_len + r->items[item].net_base, sizeof(uint32_t) * len.size(),
+                  cudaMemcpyDeviceToHost));
+    std::vector<int64_t> w((size_t)G), b((size_t)G);
+    for (int32_t q = 0; q < G; q++) {
+        const GateRec &g = n->recs[q];
+        int64_t x = 64;
+        for (int k = 0; k < g.k; k++) x += len[g.fin[k]];
+        w[q] = b[q] = x;
+    }
+    for (int32_t q = G - 1; q >= 0; q--) {   // readers come later in level order
+        const GateRec &g = n->recs[q];
+        for (int k = 0; k < g.k; k++)
+            if (g.fin[k] >= P) {
+                const int32_t f = g.fin[k] - P;
+                b[f] = std::max(b[f], w[f] + b[q]);
+            }
+    }
+    std::vector<int32_t> order((size_t)G);
+    for (int32_t q = 0; q < G; q++) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return b[x] > b[y]; });
+    std::vector<GateRec> recs((size_t)std::max(G, 1));
+    for (int32_t q = 0; q < G; q++) recs[q] = n->recs[order[q]];
+    GateRec *d = nullptr;
+    rc = dalloc_n(c, &d, recs.size());
+    if (rc) return rc;
+    n->plans.push_back(d);
+    CK(cudaMemcpy(d, recs.data(), sizeof(GateRec) * recs.size(), cudaMemcpyHostToDevice));
+    n->d_plan = d;
     return GLS_OK;
 }
 

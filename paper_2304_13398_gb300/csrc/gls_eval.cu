@@ -808,17 +808,26 @@ __device__ __forceinline__ void eval_variant(const GateRec &gr, const RunDev &r,
 }
 
 // Gate record of work index g.  With rep > 1 replicas of one netlist the work
-// order is level by level and, inside a level, replica by replica; L is the
-// caller's running level hint (work indices only grow per warp) and the net
-// ids of replica i are shifted by i * rep_nets.
+// order is level by level and, inside a level, replica by replica (L is the
+// caller's running level hint: work indices only grow per warp), or, for
+// records in a planned order, record by record and replica by replica; the
+// net ids of replica i are shifted by i * rep_nets.
 __device__ __forceinline__ GateRec fetch_gate(const GateRec *__restrict__ gates, const RunDev &r, int64_t g,
                                               int32_t &L) {
     if (r.rep <= 1) return gates[g];
-    while (g >= (int64_t)r.rep * __ldg(r.lb + L + 1)) L++;
-    const int32_t b = __ldg(r.lb + L), cnt = __ldg(r.lb + L + 1) - b;
-    const int64_t off = g - (int64_t)r.rep * b;
-    const int64_t item = off / cnt;
-    GateRec gr = gates[b + (int32_t)(off - item * cnt)];
+    int64_t item;
+    GateRec gr;
+    if (r.planned) {
+        const int64_t q = g / r.rep;
+        item = g - q * r.rep;
+        gr = gates[q];
+    } else {
+        while (g >= (int64_t)r.rep * __ldg(r.lb + L + 1)) L++;
+        const int32_t b = __ldg(r.lb + L), cnt = __ldg(r.lb + L + 1) - b;
+        const int64_t off = g - (int64_t)r.rep * b;
+        item = off / cnt;
+        gr = gates[b + (int32_t)(off - item * cnt)];
+    }
     const int32_t sh = (int32_t)(item * r.rep_nets);
 #pragma unroll
     for (int k = 0; k < 3; k++) gr.fin[k] += sh;

@@ -54,6 +54,9 @@ struct RunDev {
     int32_t rep;
     int64_t rep_nets;
     const int32_t *lb;
+    // planned order (dependency schedule): the records are in a planned
+    // topological order and work index g is record g / rep of replica g % rep
+    int32_t planned;
     unsigned long long *pi_total;   // primary-input transitions of the run (after time limits)
 };
 

@@ -45,6 +45,7 @@ SIGNATURES = [
     ("gls_rerun", ctypes.c_int, [P, i32, P]),
     ("gls_run_query", ctypes.c_int, [P, i32]),
     ("gls_run_info", ctypes.c_int, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+    ("gls_plan_order", ctypes.c_int, [P, i32, i32, i32]),
     ("gls_run_stats", ctypes.c_int, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]),
     ("gls_read_waveform", ctypes.c_int, [P, i32, i32, P, P, i64, ctypes.POINTER(i64)]),
     ("gls_read_all", ctypes.c_int, [P, i32, P, P, i64]),
@@ -255,6 +256,11 @@ class Context:
         d, c = ctypes.c_int64(0), ctypes.c_int64(0)
         self._ck(self.lib.gls_run_info(self.h, run_id, ctypes.byref(d), ctypes.byref(c)))
         return d.value, c.value
+
+    def plan_order(self, netlist_id: int, run_id: int = -1, item: int = 0):
+        """Critical-path-first dependency order for netlist_id from the net
+        activity of a finished run (run_id = -1: back to level order)."""
+        self._ck(self.lib.gls_plan_order(self.h, netlist_id, run_id, item))
 
     def run_stats(self, run_id: int) -> RunStats:
         tot, ms = ctypes.c_int64(0), ctypes.c_double(0.0)
