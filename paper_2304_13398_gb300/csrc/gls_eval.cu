@@ -60,10 +60,15 @@ template <int CH>
 struct __align__(16) WarpSmem {
     static constexpr int WIN = CH + 8;     // aligned lead (<= 3) + CH + sentinel, multiple of 4
     uint32_t win[2][3][WIN];  // double-buffered pin windows
-    uint32_t B[2 * CH + 4];   // pins a+b merged (3-input cells), sentinel-terminated
-    uint16_t Binfo[2 * CH + 8];   // source of B[i]: pin b flag (bit 15) | index in its window (+ read pad)
     uint32_t cand[3 * CH];    // per-lane stacks of scheduled transitions (t_r << 2 | v)
-    uint32_t Q[PCAP + 3 * CH];  // carried transitions (front) + this chunk's survivors
+    // Q: carried transitions (front, at most PCAP) + this chunk's survivors
+    // (at most 3 CH).  The survivors are written only after the walk, so the
+    // part past PCAP also holds the 3-input cells' merged pins a+b during the
+    // walk: B (2 CH + 4 words, sentinel-terminated) and Binfo (source of B[i]:
+    // pin b flag (bit 15) | index in its window; 2 CH + 8 halves).
+    uint32_t Q[PCAP + 3 * CH + 8];
+    __device__ __forceinline__ uint32_t *B() { return Q + PCAP; }
+    __device__ __forceinline__ uint16_t *Binfo() { return reinterpret_cast<uint16_t *>(Q + PCAP + 2 * CH + 4); }
 };
 
 // Running state of one gate's output between chunks.
@@ -373,13 +378,13 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
             uint32_t hl = A[0][i], hr = A[1][j];
             for (int s = d0; s < d1; s++) {
                 const bool tl = hl <= (hr | 3u);
-                sm.B[s] = tl ? hl : hr;
-                sm.Binfo[s] = tl ? (uint16_t)i : (uint16_t)(0x8000u | (uint32_t)j);
+                sm.B()[s] = tl ? hl : hr;
+                sm.Binfo()[s] = tl ? (uint16_t)i : (uint16_t)(0x8000u | (uint32_t)j);
                 if (tl) { i++; hl = A[0][i]; } else { j++; hr = A[1][j]; }
             }
-            if (lane == 0) sm.B[M1] = EINF;
+            if (lane == 0) sm.B()[M1] = EINF;
             __syncwarp();
-            L = sm.B;
+            L = sm.B();
             nL = M1;
         }
         const int M = nL + nR;
@@ -414,7 +419,7 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
             if (K == 3) {
                 if (i == 0) { c0 = 0; c1 = 0; }
                 else {
-                    const uint32_t inf = sm.Binfo[i - 1], idx = inf & 0x7FFFu;
+                    const uint32_t inf = sm.Binfo()[i - 1], idx = inf & 0x7FFFu;
                     if (inf & 0x8000u) { c1 = (int)idx + 1; c0 = i - c1; }
                     else { c0 = (int)idx + 1; c1 = i - c0; }
                 }
@@ -431,7 +436,7 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
                     ltp[p] = e >> 2;
                 }
             uint32_t hl = L[i], hr = R[j];
-            uint32_t hinfo = K == 3 ? sm.Binfo[i] : 0u;   // source of the L head (3-pin cells)
+            uint32_t hinfo = K == 3 ? sm.Binfo()[i] : 0u;   // source of the L head (3-pin cells)
             uint32_t Fprev = 0;
             uint32_t grp = 0;   // pins with a transition at the current timestamp
             if (d0 < d1) {
@@ -459,7 +464,7 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
                 const uint32_t y = tl ? L[i] : R[s + 1 - i];
                 hl = tl ? y : hl;
                 hr = tl ? hr : y;
-                if (K == 3) hinfo = sm.Binfo[i];
+                if (K == 3) hinfo = sm.Binfo()[i];
                 const uint32_t t = e >> 2;
                 st = setpin(st, (int)pin, e & 3u);
                 grp = (gend ? 0u : grp) | (1u << pin);
@@ -852,13 +857,16 @@ __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin,
     }
 }
 
-// Algorithm 1 without level barriers: gates are handed out in level order, so
-// every fanin gate of a handed-out gate was handed out earlier to a running
-// warp and the waits always end (the bound only guards against faults).
+// Algorithm 1 without level barriers: gates are handed out in a topological
+// order (level order, or a planned critical-path-first order), so every fanin
+// gate of a handed-out gate was handed out earlier to a running warp and the
+// waits always end (the bound only guards against faults).  72 registers a
+// thread let 28 warps of the 128-transition windowed variant share an SM
+// (shared memory admits 7 CTAs of 4 warps).
 // Completion flags are per net: primary inputs start done, a gate's output
 // net is released once its waveform and descriptor are written.
 template <int V>
-__global__ void dependency_kernel(const GateRec *__restrict__ gates, int32_t n_gates, int32_t ctr_slot, RunDev r) {
+__global__ void __maxnreg__(72) dependency_kernel(const GateRec *__restrict__ gates, int32_t n_gates, int32_t ctr_slot, RunDev r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t L = 1;
