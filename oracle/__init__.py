@@ -19,7 +19,9 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   sim_levelized          equals sim_event (independent code) on seeded
                          random netlists; settle values equal static_eval;
                          BUF/INV chain closed forms; waveform invariants and
-                         the Eq. 2 bound.
+                         the Eq. 2 bound; translation of the stimulus by more
+                         than 2^32 ps translates every waveform (times are
+                         64-bit throughout).
   sim_event              same pins as sim_levelized.
   static_eval            hand-computed settle values of small circuits.
 """
@@ -206,7 +208,7 @@ class OracleError(RuntimeError):
 
 def sim_levelized(nl, st, nthreads: int = 1) -> Result:
     n_pi, G, typ, fo, fn, dr, df = _net(nl)
-    so, stt, sv = _c(st.off, np.int64), _c(st.t, np.int32), _c(st.v, np.uint8)
+    so, stt, sv = _c(st.off, np.int64), _c(st.t, np.int64), _c(st.v, np.uint8)
     h = P()
     rc = _load().oracle_sim_levelized(n_pi, G, _p(typ), _p(fo), _p(fn), _p(dr), _p(df),
                                       _p(so), _p(stt), _p(sv), nthreads, ctypes.byref(h))
@@ -217,7 +219,7 @@ def sim_levelized(nl, st, nthreads: int = 1) -> Result:
 
 def sim_event(nl, st) -> Result:
     n_pi, G, typ, fo, fn, dr, df = _net(nl)
-    so, stt, sv = _c(st.off, np.int64), _c(st.t, np.int32), _c(st.v, np.uint8)
+    so, stt, sv = _c(st.off, np.int64), _c(st.t, np.int64), _c(st.v, np.uint8)
     h = P()
     rc = _load().oracle_sim_event(n_pi, G, _p(typ), _p(fo), _p(fn), _p(dr), _p(df),
                                   _p(so), _p(stt), _p(sv), ctypes.byref(h))
@@ -241,7 +243,7 @@ def check_gates(nl, off, t, v, g0: int = 0, g1: int | None = None, nthreads: int
     oracle's evaluation of their fanin waveforms taken from the same arrays."""
     n_pi, G, typ, fo, fn, dr, df = _net(nl)
     g1 = G if g1 is None else g1
-    off, t, v = _c(off, np.int64), _c(t, np.int32), _c(v, np.uint8)
+    off, t, v = _c(off, np.int64), _c(t, np.int64), _c(v, np.uint8)
     first = ctypes.c_int64(-1)
     bad = _load().oracle_check_gates(n_pi, G, _p(typ), _p(fo), _p(fn), _p(dr), _p(df),
                                      _p(off), _p(t), _p(v), g0, g1, nthreads, ctypes.byref(first))

@@ -320,7 +320,7 @@ static int topo_order(int32_t n_pi, int32_t G, const int32_t *fanin_off, const i
     return tail == G ? 0 : -2;
 }
 
-static void load_pis(wave_t *w, int32_t n_pi, const int64_t *soff, const int32_t *st, const uint8_t *sv) {
+static void load_pis(wave_t *w, int32_t n_pi, const int64_t *soff, const int64_t *st, const uint8_t *sv) {
     for (int32_t i = 0; i < n_pi; i++)
         for (int64_t e = soff[i]; e < soff[i + 1]; e++) wave_push(&w[i], st[e], sv[e]);
 }
@@ -332,7 +332,7 @@ static void load_pis(wave_t *w, int32_t n_pi, const int64_t *soff, const int32_t
  */
 int oracle_sim_levelized(int32_t n_pi, int32_t G, const uint8_t *type, const int32_t *fanin_off,
                          const int32_t *fanin_net, const int32_t *d_rise, const int32_t *d_fall,
-                         const int64_t *soff, const int32_t *st, const uint8_t *sv, int nthreads,
+                         const int64_t *soff, const int64_t *st, const uint8_t *sv, int nthreads,
                          oracle_result **out) {
     *out = NULL;
     if (check_netlist(n_pi, G, type, fanin_off, fanin_net, d_rise, d_fall)) return -1;
@@ -474,7 +474,7 @@ static int pend_push(pend_t *q, int64_t t, uint8_t v, int64_t seq) {
  */
 int oracle_sim_event(int32_t n_pi, int32_t G, const uint8_t *type, const int32_t *fanin_off,
                      const int32_t *fanin_net, const int32_t *d_rise, const int32_t *d_fall,
-                     const int64_t *soff, const int32_t *st, const uint8_t *sv, oracle_result **out) {
+                     const int64_t *soff, const int64_t *st, const uint8_t *sv, oracle_result **out) {
     *out = NULL;
     if (check_netlist(n_pi, G, type, fanin_off, fanin_net, d_rise, d_fall)) return -1;
     int64_t N = (int64_t)n_pi + G;
@@ -606,7 +606,7 @@ int oracle_static_eval(int32_t n_pi, int32_t G, const uint8_t *type, const int32
  */
 int64_t oracle_check_gates(int32_t n_pi, int32_t G, const uint8_t *type, const int32_t *fanin_off,
                            const int32_t *fanin_net, const int32_t *d_rise, const int32_t *d_fall,
-                           const int64_t *off, const int32_t *t, const uint8_t *v,
+                           const int64_t *off, const int64_t *t, const uint8_t *v,
                            int32_t g0, int32_t g1, int nthreads, int64_t *first_bad) {
     int64_t bad = 0, first = INT64_MAX;
     (void)G;

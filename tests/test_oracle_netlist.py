@@ -144,3 +144,21 @@ def test_check_gates_detects_planted_mistakes():
     v_bad[e] = 1 - v_bad[e] if v_bad[e] in (0, 1) else 0
     bad, first = oracle.check_gates(nl, r.off, t_bad, v_bad)
     assert bad >= 1 and first <= g
+
+
+def test_time_translation_beyond_32_bits():
+    """The method depends on time differences only (every net is X before its
+    first transition, delays add to event times, Eq. 1 compares times), so
+    shifting the whole stimulus by D shifts every waveform by D.  With D past
+    2^32 this pins the oracle's 64-bit time path, which the long-duration
+    (time-sliced) runs are checked against."""
+    nl = synth.make_netlist(10, 300, 9, fanout="pareto", d_min=5, d_max=200, seed=13)
+    st = synth.make_stimulus(10, mean=60, window=30_000, seed=14)
+    D = 3 * (1 << 31) + 12345
+    st64 = synth.Stimulus(st.off.copy(), st.t.astype(np.int64) + D, st.v.copy())
+    for sim in (oracle.sim_event, lambda a, b: oracle.sim_levelized(a, b, nthreads=2)):
+        base, far = sim(nl, st), sim(nl, st64)
+        np.testing.assert_array_equal(base.off, far.off)
+        np.testing.assert_array_equal(base.t + D, far.t)
+        np.testing.assert_array_equal(base.v, far.v)
+    assert oracle.check_gates(nl, far.off, far.t, far.v) == (0, -1)
