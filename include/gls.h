@@ -246,6 +246,60 @@ int gls_read_waveform(gls_ctx *ctx, int32_t run_id, int32_t net, int32_t *t, uin
  */
 int gls_read_all(gls_ctx *ctx, int32_t run_id, int64_t *off, uint32_t *packed, int64_t cap);
 
+/*
+ * ---- Task division over time and 64-bit times ----------------------------
+ *
+ * A stimulus may run longer than the 2^30 - 1 ps a device transition holds
+ * (Table 2's longest re-simulation runs to about 3e9 ps), and its waveforms
+ * need not fit in HBM at once: a sliced run cuts the stimulus at
+ * T_k = k * slice_ps and evaluates the slices in order, each in its own local
+ * time, carrying every gate's state across each boundary (its input pin
+ * values, its last output value, and the transitions it has scheduled at or
+ * after the boundary, which later inputs may still cancel by Eq. 1).  A
+ * transition scheduled before a boundary is final then, so the slices'
+ * outputs, concatenated, are exactly the unsliced waveforms.  Each slice's
+ * waveforms are copied to host memory as the slice completes; device memory
+ * holds one slice's transitions, the stimulus and 2 * (4 + 4 * 256) bytes of
+ * gate state per net.
+ */
+
+/* Load a stimulus with 64-bit times: like gls_load_stimulus, with
+   0 <= t < 2^62 (checked on the host, GLS_ESTIM).  Usable by sliced runs
+   only (other runs give GLS_EINVAL). */
+int gls_load_stimulus64(gls_ctx *ctx, int32_t n_pi, const int64_t *off, const int64_t *t,
+                        const uint8_t *v, int32_t *stim_id);
+
+/*
+ * Simulate netlist_id under stim_id (32- or 64-bit times) in time slices of
+ * slice_ps picoseconds; synchronous: returns once every slice is evaluated and
+ * copied to host memory.  The last slice runs to the end of all activity.
+ * The windowed kernels only (GLS_EINVAL with GLS_KERNEL_SEGMENTED); either
+ * schedule and a planned order apply.  arena_events sizes one slice's event
+ * arena (0: about 256 words per stimulus transition of an average slice); a
+ * slice that overflows it is evaluated again with a larger arena.
+ * GLS_ERANGE when slice_ps + the longest path delay reaches 2^30 - 1, or when a
+ * gate carries more than 256 scheduled transitions across a boundary;
+ * GLS_EINVAL for more than 2^20 slices.  gls_run_stats reports the total
+ * output transitions and the summed device time of the slices' gate kernels;
+ * gls_rerun evaluates every slice again (synchronously); gls_read_all,
+ * gls_read_item and gls_read_waveform give GLS_EINVAL for sliced runs.
+ */
+int gls_simulate_sliced(gls_ctx *ctx, int32_t netlist_id, int32_t stim_id, int64_t slice_ps,
+                        int64_t arena_events, void *cuda_stream, int32_t *run_id);
+
+/* Number of slices a sliced run was evaluated in (0 for other runs). */
+int gls_run_slices(gls_ctx *ctx, int32_t run_id, int32_t *n_slices);
+
+/* Every net's waveform of a sliced run, in net id order: off[n_nets + 1]
+   (always filled), 64-bit times t[cap] and values v[cap].  GLS_EOVERFLOW if
+   cap is below the total.  Host memory only. */
+int gls_read_all64(gls_ctx *ctx, int32_t run_id, int64_t *off, int64_t *t, uint8_t *v, int64_t cap);
+
+/* One net's waveform of a sliced run: *n_out always receives its length;
+   GLS_EOVERFLOW if cap is smaller (nothing copied). */
+int gls_read_waveform64(gls_ctx *ctx, int32_t run_id, int32_t net, int64_t *t, uint8_t *v, int64_t cap,
+                        int64_t *n_out);
+
 /* Context options (gls_set_option); they apply to runs created afterwards. */
 typedef enum gls_option {
     GLS_OPT_SCHEDULE = 1,       /* GLS_SCHEDULE_LEVELS or GLS_SCHEDULE_DEPENDENCY (default)  */

@@ -203,6 +203,28 @@ int check_stimulus_host(int32_t n_pi, const int64_t *off, const int32_t *t, cons
     return GLS_OK;
 }
 
+// The same rules for 64-bit times: 0 <= t < 2^62.
+int check_stimulus64_host(int32_t n_pi, const int64_t *off, const int64_t *t, const uint8_t *v, int64_t *max_t) {
+    if (n_pi < 0 || !off) return fail(GLS_EINVAL, "bad stimulus arguments");
+    if (off[0] != 0) return fail(GLS_ESTIM, "off[0] must be 0");
+    for (int32_t i = 0; i < n_pi; i++)
+        if (off[i + 1] < off[i]) return fail(GLS_ESTIM, "off not monotone at PI %d", i);
+    if (off[n_pi] > 0 && (!t || !v)) return fail(GLS_EINVAL, "NULL stimulus arrays");
+    if (off[n_pi] >= ((int64_t)1 << 32)) return fail(GLS_ESTIM, "more than 2^32 stimulus transitions");
+    int64_t mx = 0;
+    for (int32_t i = 0; i < n_pi; i++)
+        for (int64_t e = off[i]; e < off[i + 1]; e++) {
+            if (t[e] < 0 || t[e] >= ((int64_t)1 << 62))
+                return fail(GLS_ESTIM, "PI %d: time %lld out of [0, 2^62)", i, (long long)t[e]);
+            if (v[e] > 3) return fail(GLS_ESTIM, "PI %d: value %d", i, v[e]);
+            if (e > off[i] && t[e] <= t[e - 1]) return fail(GLS_ESTIM, "PI %d: times not increasing", i);
+            if (e > off[i] && v[e] == v[e - 1]) return fail(GLS_ESTIM, "PI %d: repeated value", i);
+            mx = std::max(mx, t[e]);
+        }
+    *max_t = mx;
+    return GLS_OK;
+}
+
 // ---- objects --------------------------------------------------------------
 struct DevBuf {
     void *p = nullptr;
@@ -225,6 +247,9 @@ struct StimObj {
     int32_t n_pi = 0;
     int64_t n_events = 0, cap_events = 0;
     uint32_t max_time = 0;
+    bool wide = false;                 // 64-bit times (gls_load_stimulus64): sliced runs only
+    int64_t max_time64 = 0;
+    int64_t *d_t64 = nullptr;
     int64_t *d_off = nullptr;
     int32_t *d_t = nullptr;
     uint8_t *d_v = nullptr;
@@ -259,6 +284,19 @@ struct RunObj {
     uint32_t *d_gather = nullptr;
     int64_t gather_cap = 0;
     int schedule = 0;
+    // time-sliced runs (task division over time)
+    int64_t slice_ps = 0;               // 0: not sliced
+    uint32_t *d_slice_packed = nullptr; // one slice's primary-input transitions
+    uint32_t *d_st[2] = {nullptr, nullptr};    // gate state at slice boundaries (double-buffered)
+    uint32_t *d_pend[2] = {nullptr, nullptr};  // pending transitions, kPendCap per net
+    struct Slice {
+        int64_t t0;                     // start of the slice (local time 0)
+        std::vector<int64_t> off;       // [n_nets + 1] caller net order
+        std::vector<uint32_t> packed;   // slice-local (t << 2) | v
+    };
+    std::vector<Slice> slices;
+    int64_t sliced_total = 0, sliced_demand = 0;
+    double sliced_ms = 0.0;
 };
 
 }  // namespace
@@ -379,6 +417,7 @@ void free_stim(gls_ctx *c, StimObj *s) {
     dfree(c, s->d_t);
     dfree(c, s->d_v);
     dfree(c, s->d_packed);
+    dfree(c, s->d_t64);
 }
 void free_run(gls_ctx *c, RunObj *r) {
     if (r->exec) cudaGraphExecDestroy(r->exec);
@@ -397,6 +436,11 @@ void free_run(gls_ctx *c, RunObj *r) {
     dfree(c, r->d_off);
     dfree(c, r->d_scan_tmp);
     dfree(c, r->d_gather);
+    dfree(c, r->d_slice_packed);
+    for (int k = 0; k < 2; k++) {
+        dfree(c, r->d_st[k]);
+        dfree(c, r->d_pend[k]);
+    }
 }
 
 cudaStream_t pick_stream(gls_ctx *c, void *s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
@@ -437,6 +481,18 @@ RunObj *find_run(gls_ctx *c, int32_t id) {
     return it == c->runs.end() ? nullptr : it->second.get();
 }
 
+// The gate kernels of one evaluation: one persistent launch (dependency
+// schedule) or one launch per level.
+cudaError_t launch_gates(gls_ctx *c, const RunObj *r, const RunDev &dev, cudaStream_t cs) {
+    if (r->schedule == GLS_SCHEDULE_DEPENDENCY) return launch_dependency(r->d_gates, r->n_gates, r->depth, dev, c->cfg, cs);
+    cudaError_t e = cudaSuccess;
+    for (int32_t L = 1; L <= r->depth && e == cudaSuccess; L++) {
+        const int32_t b = r->level_begin[L], cnt = r->level_begin[L + 1] - b;
+        e = launch_level(r->d_gates, b, cnt, L - 1, dev, c->cfg, cs);
+    }
+    return e;
+}
+
 int build_run_graph(gls_ctx *c, RunObj *r) {
     cudaGraph_t graph = nullptr;
     const bool dep = r->schedule == GLS_SCHEDULE_DEPENDENCY;
@@ -455,14 +511,7 @@ int build_run_graph(gls_ctx *c, RunObj *r) {
                            dep ? r->dev.done : nullptr, r->d_pi_total, cs);
     }
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(r->ev0, cs, cudaEventRecordExternal);
-    if (dep) {
-        if (e == cudaSuccess) e = launch_dependency(r->d_gates, r->n_gates, r->depth, r->dev, c->cfg, cs);
-    } else {
-        for (int32_t L = 1; L <= r->depth && e == cudaSuccess; L++) {
-            const int32_t b = r->level_begin[L], cnt = r->level_begin[L + 1] - b;
-            e = launch_level(r->d_gates, b, cnt, L - 1, r->dev, c->cfg, cs);
-        }
-    }
+    if (e == cudaSuccess) e = launch_gates(c, r, r->dev, cs);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(r->ev1, cs, cudaEventRecordExternal);
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -503,9 +552,15 @@ int items_time_range_check(gls_ctx *c, const RunObj *r) {
 // Validate the instances, lay out their nets and gates, allocate the store and
 // capture the run's graph; the run is launched by the caller.
 int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, const int32_t *t_limits,
-               int32_t n_items, int64_t arena_events, std::unique_ptr<RunObj> &out) {
+               int32_t n_items, int64_t arena_events, std::unique_ptr<RunObj> &out, int64_t slice_ps = 0) {
     auto r = std::make_unique<RunObj>();
     r->schedule = c->schedule;
+    r->slice_ps = slice_ps;
+    if (slice_ps > 0) {
+        if (n_items != 1) return fail(GLS_EINVAL, "a sliced run has one item");
+        if (c->cfg.variant == kVariantSegmented)
+            return fail(GLS_EINVAL, "sliced runs use the windowed kernels (GLS_KERNEL_WINDOWED or _WIDE)");
+    }
     int64_t stim_events = 0, base = 0;
     for (int32_t i = 0; i < n_items; i++) {
         NetlistObj *n = find_netlist(c, netlist_ids[i]);
@@ -513,8 +568,18 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
         if (!n) return fail(GLS_EINVAL, "item %d: unknown netlist id %d", i, netlist_ids[i]);
         if (!s) return fail(GLS_EINVAL, "item %d: unknown stimulus id %d", i, stim_ids[i]);
         if (s->n_pi != n->n_pi) return fail(GLS_EINVAL, "item %d: stimulus has %d PIs, netlist %d", i, s->n_pi, n->n_pi);
-        int rc = time_range_check(n, s);
-        if (rc) return rc;
+        if (slice_ps > 0) {
+            // slice-local times: inputs below slice_ps, outputs below slice_ps + the longest path
+            if (slice_ps + n->lv.max_path_delay >= (int64_t)kTimeLimit)
+                return fail(GLS_ERANGE, "slice of %lld ps + longest path delay %lld reaches 2^30-1",
+                            (long long)slice_ps, (long long)n->lv.max_path_delay);
+            const int64_t mt = s->wide ? s->max_time64 : (int64_t)s->max_time;
+            if (mt / slice_ps >= (1 << 20)) return fail(GLS_EINVAL, "more than 2^20 slices of %lld ps", (long long)slice_ps);
+        } else {
+            if (s->wide) return fail(GLS_EINVAL, "item %d: a stimulus with 64-bit times runs only in time slices", i);
+            int rc = time_range_check(n, s);
+            if (rc) return rc;
+        }
         uint32_t tl = kTimeInf;
         if (t_limits) {
             if (t_limits[i] < 0) return fail(GLS_EINVAL, "item %d: negative time limit", i);
@@ -578,6 +643,11 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
         uint64_t meta = (uint64_t)r->n_nets * 16 + (uint64_t)r->depth * 4 + 4096;
         uint64_t cap = left > meta ? (left - meta) / 2 / 4 : 0;
         uint64_t want = 256ull * (uint64_t)stim_events + (1ull << 20);
+        if (slice_ps > 0) {   // about one slice's share; a slice that overflows is rerun with more
+            const StimObj *s = find_stim(c, stim_ids[0]);
+            const int64_t mt = s->wide ? s->max_time64 : (int64_t)s->max_time;
+            want = 256ull * (uint64_t)(stim_events / (mt / slice_ps + 1) + 1) + (1ull << 20);
+        }
         arena_events = (int64_t)std::min(cap, want);
     }
     const int64_t N = r->n_nets;
@@ -599,11 +669,22 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
     if (!rc) rc = dalloc_n(c, &r->d_pi_total, 1);
     if (rc) { free_run(c, r.get()); return rc; }
     r->dev.pi_total = r->d_pi_total;
+    if (slice_ps > 0) {
+        const StimObj *s = find_stim(c, stim_ids[0]);
+        rc = dalloc_n(c, &r->d_slice_packed, (size_t)stim_words(s->cap_events, s->n_pi));
+        for (int k = 0; k < 2 && !rc; k++) {
+            rc = dalloc_n(c, &r->d_st[k], (size_t)std::max<int64_t>(N, 1));
+            if (!rc) rc = dalloc_n(c, &r->d_pend[k], (size_t)std::max<int64_t>(N, 1) * kPendCap);
+        }
+        if (rc) { free_run(c, r.get()); return rc; }
+    }
     cudaError_t e = cudaEventCreate(&r->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
     if (e != cudaSuccess) { free_run(c, r.get()); return fail(GLS_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e)); }
-    rc = build_run_graph(c, r.get());
-    if (rc) { free_run(c, r.get()); return rc; }
+    if (slice_ps == 0) {
+        rc = build_run_graph(c, r.get());
+        if (rc) { free_run(c, r.get()); return rc; }
+    }
     out = std::move(r);
     return GLS_OK;
 }
@@ -848,6 +929,7 @@ int gls_update_stimulus(gls_ctx *c, int32_t stim_id, const int64_t *off, const i
     if (!c) return fail(GLS_EINVAL, "NULL context");
     StimObj *s = find_stim(c, stim_id);
     if (!s) return fail(GLS_EINVAL, "unknown stimulus id %d", stim_id);
+    if (s->wide) return fail(GLS_EINVAL, "stimulus %d has 64-bit times; load a new one", stim_id);
     CK(cudaSetDevice(c->device));
     int rc = check_stimulus_host(s->n_pi, off, t, v, false);
     if (rc) return rc;
@@ -884,10 +966,20 @@ int gls_simulate_batch(gls_ctx *c, int32_t n_items, const int32_t *netlist_ids, 
     }
 }
 
+int run_sliced(gls_ctx *c, RunObj *r, cudaStream_t cs);
+
 int gls_rerun(gls_ctx *c, int32_t run_id, void *cuda_stream) {
     if (!c) return fail(GLS_EINVAL, "NULL context");
     RunObj *r = find_run(c, run_id);
     if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    if (r->slice_ps > 0) {
+        CK(cudaSetDevice(c->device));
+        try {
+            return run_sliced(c, r, pick_stream(c, cuda_stream));
+        } catch (const std::bad_alloc &) {
+            return fail(GLS_ENOMEM, "host allocation failed");
+        }
+    }
     int rc = items_time_range_check(c, r);
     if (rc) return rc;
     CK(cudaSetDevice(c->device));
@@ -914,16 +1006,28 @@ int gls_run_info(gls_ctx *c, int32_t run_id, int64_t *arena_demand, int64_t *are
     CK(cudaEventSynchronize(r->ev1));
     unsigned long long top = 0;
     CK(cudaMemcpy(&top, r->dev.arena_top, sizeof top, cudaMemcpyDeviceToHost));
+    if (r->slice_ps > 0) top = (unsigned long long)r->sliced_demand;   // largest slice
     if (arena_demand) *arena_demand = (int64_t)top;
     if (arena_capacity) *arena_capacity = (int64_t)r->dev.arena_cap;
     return GLS_OK;
 }
+
+int run_stats_impl(gls_ctx *c, RunObj *r, int64_t *total_events, double *kernel_ms);
 
 int gls_run_stats(gls_ctx *c, int32_t run_id, int64_t *total_events, double *kernel_ms) {
     if (!c) return fail(GLS_EINVAL, "NULL context");
     RunObj *r = find_run(c, run_id);
     if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
     CK(cudaSetDevice(c->device));
+    if (r->slice_ps > 0) {   // evaluated synchronously; errors were returned then
+        if (total_events) *total_events = r->sliced_total;
+        if (kernel_ms) *kernel_ms = r->sliced_ms;
+        return GLS_OK;
+    }
+    return run_stats_impl(c, r, total_events, kernel_ms);
+}
+
+int run_stats_impl(gls_ctx *c, RunObj *r, int64_t *total_events, double *kernel_ms) {
     CK(cudaEventSynchronize(r->ev1));
     uint32_t status = 0;
     unsigned long long top = 0, sum = 0;
@@ -950,6 +1054,86 @@ int gls_run_stats(gls_ctx *c, int32_t run_id, int64_t *total_events, double *ker
     if (status & kStTimeRange) return fail(GLS_ERANGE, "a computed time reached 2^30-1");
     if (status & kStTimeout) return fail(GLS_ETIMEOUT, "a wait for a fanin gate exceeded %.3f s",
                                          (double)r->dev.wait_limit_ns * 1e-9);
+    return GLS_OK;
+}
+
+// Task division over time: the stimulus is cut at T_k = k * slice_ps and the
+// slices are evaluated one after the other, each on the primary-input
+// transitions inside it, in slice-local time.  Every gate carries its state
+// across a boundary (input pin values, last output value, the scheduled
+// transitions at or past the boundary, which later inputs may still cancel
+// by Eq. 1); a transition scheduled before the boundary is final, because a
+// later input can only schedule at or after boundary + dmin.  So the slices'
+// outputs, concatenated, are the unsliced waveforms.  Each slice's waveforms
+// are copied to host memory; a slice whose arena overflows is evaluated again
+// with a larger one (its input state is still intact: double-buffered).
+int run_sliced(gls_ctx *c, RunObj *r, cudaStream_t cs) {
+    const RunItem &it = r->items[0];
+    NetlistObj *n = find_netlist(c, it.netlist_id);
+    StimObj *s = find_stim(c, it.stim_id);
+    const int64_t S = r->slice_ps, N = r->n_nets;
+    const int64_t mt = s->wide ? s->max_time64 : (int64_t)s->max_time;
+    const int32_t ns = s->n_events > 0 ? (int32_t)(mt / S + 1) : 1;
+    const bool dep = r->schedule == GLS_SCHEDULE_DEPENDENCY;
+    r->slices.clear();
+    r->sliced_total = 0;
+    r->sliced_demand = 0;
+    r->sliced_ms = 0.0;
+    CK(cudaMemsetAsync(r->d_st[0], 0, sizeof(uint32_t) * (size_t)N, cs));   // start state
+    for (int32_t k = 0; k < ns; k++) {
+        const int64_t T0 = (int64_t)k * S, T1 = k == ns - 1 ? INT64_MAX : T0 + S;
+        RunDev d = r->dev;
+        d.st_in = r->d_st[k & 1];
+        d.st_out = r->d_st[(k + 1) & 1];
+        d.pend_in = r->d_pend[k & 1];
+        d.pend_out = r->d_pend[(k + 1) & 1];
+        d.slice_end = k == ns - 1 ? kTimeInf : (uint32_t)S;
+        d.slice_shift = k == 0 ? 0u : (uint32_t)S;
+        int64_t total = 0;
+        double ms = 0.0;
+        for (int attempt = 0;; attempt++) {
+            CK(cudaMemsetAsync(d.level_ctr, 0, sizeof(int32_t) * ((size_t)r->depth + 1), cs));
+            CK(cudaMemsetAsync(d.arena_top, 0, sizeof(unsigned long long), cs));
+            CK(cudaMemsetAsync(d.status, 0, sizeof(uint32_t), cs));
+            if (dep) CK(cudaMemsetAsync(d.done, 0, sizeof(uint32_t) * (size_t)N, cs));
+            CK(cudaMemsetAsync(r->d_pi_total, 0, sizeof(unsigned long long), cs));
+            CK(launch_slice_pack(s->d_off, s->wide ? nullptr : s->d_t, s->wide ? s->d_t64 : nullptr, s->d_v, n->n_pi,
+                                 T0, T1, r->d_slice_packed, d.net_ptr, d.net_len, dep ? d.done : nullptr,
+                                 r->d_pi_total, cs));
+            CK(cudaEventRecord(r->ev0, cs));
+            CK(launch_gates(c, r, d, cs));
+            CK(cudaEventRecord(r->ev1, cs));
+            const int rc = run_stats_impl(c, r, &total, &ms);
+            if (rc == GLS_OK) break;
+            if (rc != GLS_EOVERFLOW || attempt >= 8) return rc;
+            // total is a lower bound of this slice's demand: grow and evaluate it again
+            const uint64_t want = std::max<uint64_t>(2 * r->dev.arena_cap, (uint64_t)total + total / 4 + (1u << 20));
+            dfree(c, r->dev.arena);
+            r->dev.arena = nullptr;
+            r->dev.arena_cap = 0;
+            int arc = dalloc_n(c, &r->dev.arena, (size_t)want + 2 * kSlotAlign);
+            if (arc) return arc;
+            r->dev.arena_cap = want;
+            d.arena = r->dev.arena;
+            d.arena_cap = want;
+        }
+        unsigned long long top = 0;
+        CK(cudaMemcpy(&top, d.arena_top, sizeof top, cudaMemcpyDeviceToHost));
+        r->sliced_demand = std::max<int64_t>(r->sliced_demand, (int64_t)top);
+        r->sliced_total += total;
+        r->sliced_ms += ms;
+        RunObj::Slice sl;
+        sl.t0 = T0;
+        sl.off.assign((size_t)N + 1, 0);
+        int rc = read_item(c, r, 0, sl.off.data(), nullptr, 0);
+        if (rc != GLS_OK && rc != GLS_EOVERFLOW) return rc;
+        sl.packed.resize((size_t)sl.off[N]);
+        if (sl.off[N] > 0) {
+            rc = read_item(c, r, 0, sl.off.data(), sl.packed.data(), sl.off[N]);
+            if (rc) return rc;
+        }
+        r->slices.push_back(std::move(sl));
+    }
     return GLS_OK;
 }
 
@@ -1012,6 +1196,7 @@ int gls_read_waveform(gls_ctx *c, int32_t run_id, int32_t net, int32_t *t, uint8
     if (!c) return fail(GLS_EINVAL, "NULL context");
     RunObj *r = find_run(c, run_id);
     if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    if (r->slice_ps > 0) return fail(GLS_EINVAL, "run %d is sliced: read it with gls_read_waveform64", run_id);
     NetlistObj *n = find_netlist(c, r->items[0].netlist_id);
     const int64_t N = (int64_t)n->n_pi + n->n_gates;
     if (net < 0 || net >= N) return fail(GLS_EINVAL, "net %d out of range", net);
@@ -1047,6 +1232,7 @@ int gls_read_item(gls_ctx *c, int32_t run_id, int32_t item, int64_t *off, uint32
     if (!c || !off) return fail(GLS_EINVAL, "NULL argument");
     RunObj *r = find_run(c, run_id);
     if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    if (r->slice_ps > 0) return fail(GLS_EINVAL, "run %d is sliced: read it with gls_read_all64", run_id);
     CK(cudaSetDevice(c->device));
     try {
         return read_item(c, r, item, off, packed, cap);
@@ -1189,6 +1375,113 @@ int gls_release(gls_ctx *c, int32_t id) {
         return GLS_OK;
     }
     return fail(GLS_EINVAL, "unknown id %d", id);
+}
+
+
+int gls_load_stimulus64(gls_ctx *c, int32_t n_pi, const int64_t *off, const int64_t *t, const uint8_t *v,
+                        int32_t *stim_id) {
+    if (!c || !stim_id) return fail(GLS_EINVAL, "NULL argument");
+    try {
+        CK(cudaSetDevice(c->device));
+        int64_t mx = 0;
+        int rc = check_stimulus64_host(n_pi, off, t, v, &mx);
+        if (rc) return rc;
+        auto s = std::make_unique<StimObj>();
+        s->n_pi = n_pi;
+        s->wide = true;
+        s->cap_events = s->n_events = off[n_pi];
+        s->max_time64 = mx;
+        const size_t E = (size_t)std::max<int64_t>(s->cap_events, 1);
+        rc = dalloc_n(c, &s->d_off, (size_t)n_pi + 1);
+        if (!rc) rc = dalloc_n(c, &s->d_t64, E);
+        if (!rc) rc = dalloc_n(c, &s->d_v, E);
+        if (rc) { free_stim(c, s.get()); return rc; }
+        cudaError_t e = cudaMemcpy(s->d_off, off, sizeof(int64_t) * ((size_t)n_pi + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && s->n_events > 0)
+            e = cudaMemcpy(s->d_t64, t, sizeof(int64_t) * (size_t)s->n_events, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && s->n_events > 0) e = cudaMemcpy(s->d_v, v, (size_t)s->n_events, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { free_stim(c, s.get()); return fail(GLS_ECUDA, "stimulus upload: %s", cudaGetErrorString(e)); }
+        const int32_t id = c->next_id++;
+        c->stims[id] = std::move(s);
+        *stim_id = id;
+        return GLS_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(GLS_ENOMEM, "host allocation failed");
+    }
+}
+
+int gls_simulate_sliced(gls_ctx *c, int32_t netlist_id, int32_t stim_id, int64_t slice_ps, int64_t arena_events,
+                        void *cuda_stream, int32_t *run_id) {
+    if (!c || !run_id) return fail(GLS_EINVAL, "NULL argument");
+    if (slice_ps < 1) return fail(GLS_EINVAL, "slice_ps must be >= 1");
+    try {
+        CK(cudaSetDevice(c->device));
+        std::unique_ptr<RunObj> r;
+        int rc = create_run(c, &netlist_id, &stim_id, nullptr, 1, arena_events, r, slice_ps);
+        if (rc) return rc;
+        rc = run_sliced(c, r.get(), pick_stream(c, cuda_stream));
+        if (rc) { free_run(c, r.get()); return rc; }
+        const int32_t id = c->next_id++;
+        c->runs[id] = std::move(r);
+        *run_id = id;
+        return GLS_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(GLS_ENOMEM, "host allocation failed");
+    }
+}
+
+int gls_run_slices(gls_ctx *c, int32_t run_id, int32_t *n_slices) {
+    if (!c || !n_slices) return fail(GLS_EINVAL, "NULL argument");
+    RunObj *r = find_run(c, run_id);
+    if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    *n_slices = r->slice_ps > 0 ? (int32_t)r->slices.size() : 0;
+    return GLS_OK;
+}
+
+int gls_read_all64(gls_ctx *c, int32_t run_id, int64_t *off, int64_t *t, uint8_t *v, int64_t cap) {
+    if (!c || !off) return fail(GLS_EINVAL, "NULL argument");
+    RunObj *r = find_run(c, run_id);
+    if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    if (r->slice_ps == 0) return fail(GLS_EINVAL, "run %d is not sliced: read it with gls_read_all", run_id);
+    const int64_t N = r->n_nets;
+    off[0] = 0;
+    for (int64_t q = 0; q < N; q++) {
+        int64_t len = 0;
+        for (const auto &sl : r->slices) len += sl.off[q + 1] - sl.off[q];
+        off[q + 1] = off[q] + len;
+    }
+    if (off[N] > cap) return fail(GLS_EOVERFLOW, "%lld transitions, cap %lld", (long long)off[N], (long long)cap);
+    if (off[N] > 0 && (!t || !v)) return fail(GLS_EINVAL, "NULL output arrays");
+    for (int64_t q = 0; q < N; q++) {
+        int64_t o = off[q];
+        for (const auto &sl : r->slices)
+            for (int64_t e = sl.off[q]; e < sl.off[q + 1]; e++, o++) {
+                t[o] = sl.t0 + (int64_t)(sl.packed[e] >> 2);
+                v[o] = (uint8_t)(sl.packed[e] & 3u);
+            }
+    }
+    return GLS_OK;
+}
+
+int gls_read_waveform64(gls_ctx *c, int32_t run_id, int32_t net, int64_t *t, uint8_t *v, int64_t cap,
+                        int64_t *n_out) {
+    if (!c || !n_out) return fail(GLS_EINVAL, "NULL argument");
+    RunObj *r = find_run(c, run_id);
+    if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    if (r->slice_ps == 0) return fail(GLS_EINVAL, "run %d is not sliced: read it with gls_read_waveform", run_id);
+    if (net < 0 || net >= r->n_nets) return fail(GLS_EINVAL, "net %d out of range", net);
+    int64_t len = 0;
+    for (const auto &sl : r->slices) len += sl.off[net + 1] - sl.off[net];
+    *n_out = len;
+    if (len > cap) return fail(GLS_EOVERFLOW, "%lld transitions, cap %lld", (long long)len, (long long)cap);
+    if (len > 0 && (!t || !v)) return fail(GLS_EINVAL, "NULL output arrays");
+    int64_t o = 0;
+    for (const auto &sl : r->slices)
+        for (int64_t e = sl.off[net]; e < sl.off[net + 1]; e++, o++) {
+            t[o] = sl.t0 + (int64_t)(sl.packed[e] >> 2);
+            v[o] = (uint8_t)(sl.packed[e] & 3u);
+        }
+    return GLS_OK;
 }
 
 }  // extern "C"

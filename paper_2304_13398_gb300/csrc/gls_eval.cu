@@ -50,7 +50,7 @@ void set_luts(const uint64_t lut[][2], int ncells) {
 
 namespace {
 
-constexpr int PCAP = 256;               // carried (pending) transitions, > GLS_MAX_DELAY_SPREAD
+constexpr int PCAP = kPendCap;          // carried (pending) transitions, > GLS_MAX_DELAY_SPREAD
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr uint32_t EINF = 0xFFFFFFFFu;  // sentinel event; its time 2^30-1 exceeds every real time
 
@@ -284,8 +284,25 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
     for (int p = 0; p < K; p++) g.dmax = max(g.dmax, max(g.rise[p], g.fall[p]));
     const uint32_t out_net = gr.out_net;
 
-    if (bound == 0) {   // no input transition: the output stays X (Algorithm 2 starts at X)
-        if (lane == 0) { r.net_ptr[out_net] = 0; r.net_len[out_net] = 0; }
+    // state before the first input transition: pins at X, output X, nothing
+    // pending -- or, in a time slice, where the previous slice left the gate
+    uint32_t carry = 0x2Au;
+    CommitState cs{0u, kVX, 0};
+    uint32_t send = kTimeInf;   // transitions with t_r >= send stay pending
+    if (r.st_in) {
+        const uint32_t h = r.st_in[out_net];
+        carry = (h & 63u) ^ 0x2Au;
+        cs.lastV = ((h >> 8) & 3u) ^ kVX;
+        cs.np = (int)(h >> 16);
+        bound += (uint64_t)cs.np;   // each carried transition may become an output
+        send = r.slice_end;
+    }
+    if (bound == 0) {   // no input transition: the output stays as it is (X at the start, Algorithm 2)
+        if (lane == 0) {
+            r.net_ptr[out_net] = 0;
+            r.net_len[out_net] = 0;
+            if (r.st_in) r.st_out[out_net] = r.st_in[out_net];
+        }
         return;
     }
     unsigned long long base = 0;
@@ -300,19 +317,23 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         return;
     }
     uint32_t *out = r.arena + base;
+    if (cs.np > 0) {   // carried transitions, moved to this slice's local time
+        const uint32_t *pp = r.pend_in + (size_t)out_net * PCAP;
+        for (int x = lane; x < cs.np; x += 32) sm.Q[x] = pp[x] - (r.slice_shift << 2);
+        __syncwarp();
+    }
 
     // 4-value tables: K == 1 uses f(a) with b = c = X (entries 40..43),
     // K == 2 uses f(a, b) with c = X (entries 32..47), K == 3 all 64
     const uint32_t lut1 = (uint32_t)(g.lut_hi >> 16) & 0xFFu;
     const uint32_t lut2 = (uint32_t)g.lut_hi;
 
-    uint32_t carry = 0x2Au;           // pins a, b, c at X before the first transition
-    CommitState cs{0u, kVX, 0};
     uint32_t cur[3] = {0, 0, 0};
     bool failed = false;
     int b = 0;
     int lead[3] = {0, 0, 0}, n[3] = {0, 0, 0};
     bool more = issue_windows<K, CH>(sm, 0, g, cur, lead, n, lane);
+    const bool any_input = more;
 
     while (more) {
         cp_async_wait_all();
@@ -486,7 +507,7 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         }
 
         // ---- 4./5. Eq. 1 across lanes, commit, carry ----
-        const uint32_t Tfin = last ? kTimeInf : Tend + 1u + g.dmin;
+        const uint32_t Tfin = min(last ? kTimeInf : Tend + 1u + g.dmin, send);
         if (!commit_chunk<CH>(sm, lane, d0, top, Tfin, out, cs)) { failed = true; break; }
 #pragma unroll
         for (int p = 0; p < K; p++)
@@ -497,6 +518,15 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         __syncwarp();
     }
     if (failed) cp_async_wait_all();   // leave no copy in flight into this warp's buffers
+    if (r.st_in && !failed) {
+        // no input transition in this slice: settle the carried ones alone
+        if (!any_input) failed = !commit_chunk<CH>(sm, lane, 0, 0, send, out, cs);
+        if (!failed) {
+            if (lane == 0) r.st_out[out_net] = (carry ^ 0x2Au) | ((cs.lastV ^ kVX) << 8) | ((uint32_t)cs.np << 16);
+            uint32_t *pp = r.pend_out + (size_t)out_net * PCAP;
+            for (int x = lane; x < cs.np; x += 32) pp[x] = sm.Q[x];
+        }
+    }
     if (lane == 0) {
         if (failed) atomicOr(r.status, kStPendingOverflow);
         r.net_ptr[out_net] = reinterpret_cast<uint64_t>(out);

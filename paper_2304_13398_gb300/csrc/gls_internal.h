@@ -57,8 +57,22 @@ struct RunDev {
     // planned order (dependency schedule): the records are in a planned
     // topological order and work index g is record g / rep of replica g % rep
     int32_t planned;
+    // Time-sliced runs (task division over time), else null: every gate's
+    // state at the start (st_in, pend_in) and end (st_out, pend_out) of the
+    // slice, per net.  st = (input pins ^ 0x2A) | (output value ^ X) << 8 |
+    // pending count << 16, so all-zero is the start state (inputs X, output
+    // X, nothing pending); pend holds kPendCap pending transitions per net in
+    // the previous slice's local time.
+    uint32_t *st_in, *st_out, *pend_in, *pend_out;
+    uint32_t slice_end;       // local end of the slice: a t_r at or past it stays pending
+    uint32_t slice_shift;     // start of this slice minus start of the previous one
     unsigned long long *pi_total;   // primary-input transitions of the run (after time limits)
 };
+
+// Pending (scheduled, not yet final) transitions a gate carries from one
+// input chunk or time slice to the next; more than the delay spread of a
+// cell fits (GLS_MAX_DELAY_SPREAD).
+constexpr int kPendCap = 256;
 
 // Output slots are padded to whole 128-byte lines so that no two nets share a
 // cache line (a reader's L1 can then never hold a stale copy of a line that a
@@ -99,6 +113,13 @@ cudaError_t launch_level(const GateRec *d_gates, int32_t g_begin, int32_t g_coun
 cudaError_t launch_dependency(const GateRec *d_gates, int32_t n_gates, int32_t ctr_slot, const RunDev &r,
                               const LevelCfg &cfg, cudaStream_t s);
 
+// Primary-input descriptors of one time slice [T0, T1): each PI's
+// transitions in the slice, as slice-local packed transitions at the start of
+// its 16-byte-aligned slot (stim_slot) of d_packed; done flags set; pi_total
+// accumulates the slice's PI transitions.  Exactly one of t32 / t64 is set.
+cudaError_t launch_slice_pack(const int64_t *d_off, const int32_t *d_t32, const int64_t *d_t64, const uint8_t *d_v,
+                              int32_t n_pi, int64_t T0, int64_t T1, uint32_t *d_packed, uint64_t *net_ptr,
+                              uint32_t *net_len, uint32_t *done, unsigned long long *pi_total, cudaStream_t s);
 cudaError_t launch_pack_stimulus(const int64_t *d_off, const int32_t *d_t, const uint8_t *d_v, int32_t n_pi,
                                  uint32_t *d_packed, uint32_t *d_status, cudaStream_t s);
 cudaError_t launch_run_init(const int64_t *d_stim_off, const uint32_t *d_stim_packed, const RunDev &r,

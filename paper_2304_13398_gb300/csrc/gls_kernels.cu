@@ -38,6 +38,51 @@ __global__ void pack_stimulus_kernel(const int64_t *__restrict__ off, const int3
     if (lane == 0) atomicMax(status + 2, tmax);
 }
 
+// First index of a[0..n) whose time is >= T.
+template <typename TT>
+__device__ __forceinline__ int64_t first_at_or_after(const TT *a, int64_t n, int64_t T) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)a[mid] < T) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One warp per primary input: the PI's transitions in the time slice
+// [T0, T1), moved to slice-local time (t - T0 fits 30 bits, checked on the
+// host) and packed at the start of the PI's aligned slot.
+template <typename TT>
+__global__ void slice_pack_kernel(const int64_t *__restrict__ off, const TT *__restrict__ t,
+                                  const uint8_t *__restrict__ v, int32_t n_pi, int64_t T0, int64_t T1,
+                                  uint32_t *__restrict__ packed, uint64_t *net_ptr, uint32_t *net_len, uint32_t *done,
+                                  unsigned long long *pi_total) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long tot = 0;
+    for (int64_t pi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pi < n_pi; pi += warps) {
+        const int64_t a = off[pi], n = off[pi + 1] - a;
+        int64_t lo = 0, hi = 0;
+        if (lane == 0) {
+            lo = first_at_or_after(t + a, n, T0);
+            hi = first_at_or_after(t + a, n, T1);
+        }
+        lo = __shfl_sync(FULL, lo, 0);
+        hi = __shfl_sync(FULL, hi, 0);
+        uint32_t *dst = packed + stim_slot(a, pi);
+        for (int64_t e = lo + lane; e < hi; e += 32)
+            dst[e - lo] = ((uint32_t)((int64_t)t[a + e] - T0) << 2) | (v[a + e] & 3u);
+        if (lane == 0) {
+            net_ptr[pi] = reinterpret_cast<uint64_t>(dst);
+            net_len[pi] = (uint32_t)(hi - lo);
+            if (done) done[pi] = 1u;
+            tot += (unsigned long long)(hi - lo);
+        }
+    }
+    if (lane == 0 && tot) atomicAdd(pi_total, tot);
+}
+
 // PI net descriptors point into the packed stimulus; everything a run
 // accumulates (counters, status, completion flags) is reset.
 __global__ void run_init_kernel(const int64_t *__restrict__ off, const uint32_t *packed, RunDev r, int32_t n_ctr) {
@@ -179,6 +224,19 @@ cudaError_t launch_pack_stimulus(const int64_t *d_off, const int32_t *d_t, const
                                  uint32_t *d_packed, uint32_t *d_status, cudaStream_t s) {
     if (n_pi <= 0) return cudaSuccess;
     pack_stimulus_kernel<<<grid_for(n_pi, 8), 256, 0, s>>>(d_off, d_t, d_v, n_pi, d_packed, d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slice_pack(const int64_t *d_off, const int32_t *d_t32, const int64_t *d_t64, const uint8_t *d_v,
+                              int32_t n_pi, int64_t T0, int64_t T1, uint32_t *d_packed, uint64_t *net_ptr,
+                              uint32_t *net_len, uint32_t *done, unsigned long long *pi_total, cudaStream_t s) {
+    if (n_pi <= 0) return cudaSuccess;
+    if (d_t64)
+        slice_pack_kernel<int64_t><<<grid_for(n_pi, 8), 256, 0, s>>>(d_off, d_t64, d_v, n_pi, T0, T1, d_packed, net_ptr,
+                                                                     net_len, done, pi_total);
+    else
+        slice_pack_kernel<int32_t><<<grid_for(n_pi, 8), 256, 0, s>>>(d_off, d_t32, d_v, n_pi, T0, T1, d_packed, net_ptr,
+                                                                     net_len, done, pi_total);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,11 @@ SIGNATURES = [
     ("gls_run_query", ctypes.c_int, [P, i32]),
     ("gls_run_info", ctypes.c_int, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     ("gls_plan_order", ctypes.c_int, [P, i32, i32, i32]),
+    ("gls_load_stimulus64", ctypes.c_int, [P, i32, P, P, P, ctypes.POINTER(i32)]),
+    ("gls_simulate_sliced", ctypes.c_int, [P, i32, i32, i64, i64, P, ctypes.POINTER(i32)]),
+    ("gls_run_slices", ctypes.c_int, [P, i32, ctypes.POINTER(i32)]),
+    ("gls_read_all64", ctypes.c_int, [P, i32, P, P, P, i64]),
+    ("gls_read_waveform64", ctypes.c_int, [P, i32, i32, P, P, i64, ctypes.POINTER(i64)]),
     ("gls_run_stats", ctypes.c_int, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]),
     ("gls_read_waveform", ctypes.c_int, [P, i32, i32, P, P, i64, ctypes.POINTER(i64)]),
     ("gls_read_all", ctypes.c_int, [P, i32, P, P, i64]),
@@ -198,6 +203,52 @@ class Context:
         n_pi = len(off) - 1 if n_pi is None else n_pi
         self._ck(self.lib.gls_load_stimulus(self.h, n_pi, _p(off), _p(t), _p(v), ctypes.byref(sid)))
         return sid.value
+
+    def load_stimulus64(self, st, n_pi: int | None = None) -> int:
+        """A stimulus with 64-bit times (for simulate_sliced)."""
+        off, t, v = _c(st.off, np.int64), _c(st.t, np.int64), _c(st.v, np.uint8)
+        sid = ctypes.c_int32(0)
+        n_pi = len(off) - 1 if n_pi is None else n_pi
+        self._ck(self.lib.gls_load_stimulus64(self.h, n_pi, _p(off), _p(t), _p(v), ctypes.byref(sid)))
+        return sid.value
+
+    def simulate_sliced(self, netlist_id: int, stim_id: int, slice_ps: int, arena_events: int = 0,
+                        stream=None) -> int:
+        """Task division over time (synchronous); read with read_all64 / read_waveform64."""
+        rid = ctypes.c_int32(0)
+        self._ck(self.lib.gls_simulate_sliced(self.h, netlist_id, stim_id, int(slice_ps), arena_events,
+                                              _stream_handle(stream), ctypes.byref(rid)))
+        self.n_nets[rid.value] = self.n_nets[netlist_id]
+        return rid.value
+
+    def run_slices(self, run_id: int) -> int:
+        n = ctypes.c_int32(0)
+        self._ck(self.lib.gls_run_slices(self.h, run_id, ctypes.byref(n)))
+        return n.value
+
+    def read_all64(self, run_id: int):
+        """(off int64[N+1], t int64[E], v uint8[E]) of a sliced run."""
+        N = self.n_nets[run_id]
+        N = N[0] if isinstance(N, list) else N
+        off = np.zeros(N + 1, np.int64)
+        rc = self.lib.gls_read_all64(self.h, run_id, _p(off), None, None, 0)
+        if rc not in (GLS_OK, GLS_EOVERFLOW):
+            self._ck(rc)
+        E = int(off[N])
+        t = np.zeros(E, np.int64)
+        v = np.zeros(E, np.uint8)
+        self._ck(self.lib.gls_read_all64(self.h, run_id, _p(off), _p(t), _p(v), E))
+        return off, t, v
+
+    def read_waveform64(self, run_id: int, net: int):
+        n = ctypes.c_int64(0)
+        rc = self.lib.gls_read_waveform64(self.h, run_id, net, None, None, 0, ctypes.byref(n))
+        if rc not in (GLS_OK, GLS_EOVERFLOW):
+            self._ck(rc)
+        t = np.zeros(n.value, np.int64)
+        v = np.zeros(n.value, np.uint8)
+        self._ck(self.lib.gls_read_waveform64(self.h, run_id, net, _p(t), _p(v), n.value, ctypes.byref(n)))
+        return t, v
 
     def update_stimulus(self, stim_id: int, off, t, v):
         """off/t/v may be numpy arrays or (pinned) torch CPU tensors."""
