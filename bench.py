@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve", "sliced"],
                     help="plain: one 1M-gate run (the headline); batch: 64 stimulus sets + 16 netlists "
                          "in batched launches vs one at a time; serve: 200 req/s over resident netlists, "
                          "continuous batching vs plain")
@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--batch-sets", type=int, default=64)
     ap.add_argument("--batch-netlists", type=int, default=16)
     ap.add_argument("--workload", default="ind1m")
+    ap.add_argument("--slice-ps", type=int, default=1_000_000, help="sliced mode: slice length on the 1M-gate run")
+    ap.add_argument("--long-window", type=int, default=2_970_000_000,
+                    help="sliced mode: duration of the long (64-bit time) stimulus, ps")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-frac", type=float, default=0.005,
                     help="time-window fraction of the CPU-oracle sample")
@@ -526,6 +529,78 @@ def run_batch(a):
     return 0
 
 
+def run_sliced(a):
+    """Task division over time.  (1) The 1M-gate workload in slices of
+    --slice-ps against the same workload unsliced (same kernel, same order):
+    the cost of cutting.  (2) The 1M-gate netlist under a stimulus of
+    --long-window ps (64-bit times; the paper's longest re-simulation runs
+    2.97e9 ps) with the recipe's 2000 transitions per PI, in 2^29 ps slices.
+    Device time = the slices' gate kernels; wall = the whole call, including
+    each slice's copy of its waveforms to host memory."""
+    import torch
+    import paper_2304_13398_gb300 as gls
+    import synth
+    torch.cuda.set_device(0)
+    w = synth.make_workload(a.workload, seed=a.seed)
+    nl, st = w.netlist, w.stimulus
+    ctx = gls.Context(0)
+    ctx.set_kernel(a.kernel)
+    nid = ctx.load_netlist(nl)
+    order = plan_from_calibration(ctx, nid, nl, w.recipe["stim"], a.seed)
+    sid = ctx.load_stimulus(st)
+    rid = ctx.simulate(nid, sid)
+    rc, demand, _ = ctx.run_stats_raw(rid)
+    arena = 0
+    while rc == gls.gls.GLS_EOVERFLOW:
+        ctx.release(rid)
+        arena = int(demand * 1.25) + 1024
+        rid = ctx.simulate(nid, sid, arena_events=arena)
+        rc, demand, _ = ctx.run_stats_raw(rid)
+    for _ in range(3):
+        ctx.rerun(rid)
+    ctx.rerun(rid)
+    plain = ctx.run_stats(rid)
+    ctx.release(rid)
+    out = {}
+    for label, stim_id, slice_ps in [("sliced_1m", sid, a.slice_ps)]:
+        rid = ctx.simulate_sliced(nid, stim_id, slice_ps)
+        ctx.release(rid)
+        t0 = time.perf_counter()
+        rid = ctx.simulate_sliced(nid, stim_id, slice_ps)
+        wall = time.perf_counter() - t0
+        stt = ctx.run_stats(rid)
+        out[label] = {"slice_ps": slice_ps, "slices": ctx.run_slices(rid), "transitions": stt.total_events,
+                      "device_ms": stt.kernel_ms, "value": stt.total_events / (stt.kernel_ms / 1000.0),
+                      "wall_s": wall, "wall_value": stt.total_events / wall,
+                      "equal_transitions_to_unsliced": stt.total_events == plain.total_events}
+        ctx.release(rid)
+    ctx.release(sid)
+    sp = dict(w.recipe["stim"])
+    sp["window"] = int(a.long_window)
+    lst = synth.make_stimulus(nl.n_pi, seed=a.seed + 1000003, **sp)   # 64-bit times past 2^31 ps
+    lid = ctx.load_stimulus64(lst)
+    rid = ctx.simulate_sliced(nid, lid, 1 << 29)
+    stt = ctx.run_stats(rid)
+    ctx.release(rid)
+    t0 = time.perf_counter()
+    rid = ctx.simulate_sliced(nid, lid, 1 << 29)
+    wall = time.perf_counter() - t0
+    stt = ctx.run_stats(rid)
+    out["long_64bit"] = {"window_ps": int(a.long_window), "slice_ps": 1 << 29, "slices": ctx.run_slices(rid),
+                         "stimulus_transitions": int(lst.n_events), "transitions": stt.total_events,
+                         "device_ms": stt.kernel_ms, "value": stt.total_events / (stt.kernel_ms / 1000.0),
+                         "wall_s": wall, "wall_value": stt.total_events / wall}
+    ctx.release(rid)
+    ctx.close()
+    line = {"metric": "sliced output transitions/s (task division over time, 1M gates)", "unit": UNIT,
+            "mode": "sliced", "n_gpus": 1, "higher_is_better": True, "kernel": a.kernel, "gate_order": order,
+            "unsliced": {"transitions": plain.total_events, "device_ms": plain.kernel_ms,
+                         "value": plain.total_events / (plain.kernel_ms / 1000.0)},
+            **out, "data": "synthetic", "dtype": "u32 packed slice-local events, 64-bit slice origins"}
+    print(json.dumps(line))
+    return 0
+
+
 def run_serve(a):
     """Served form: a seeded Poisson request stream (200 req/s, 30 s) over 8
     resident netlists of log-uniform size (5k-5M gates), stimulus windows
@@ -582,6 +657,8 @@ def main():
         return run_batch(a)
     if a.mode == "serve":
         return run_serve(a)
+    if a.mode == "sliced":
+        return run_sliced(a)
     return run_own(a)
 
 

@@ -55,6 +55,8 @@ def _load():
         lib.synth_stim_counts.argtypes = stim_args + [P]
         lib.synth_stim_fill.restype = ctypes.c_int
         lib.synth_stim_fill.argtypes = stim_args + [P, P, P]
+        lib.synth_stim_fill64.restype = ctypes.c_int
+        lib.synth_stim_fill64.argtypes = stim_args + [P, P, P]
         _lib = lib
     return _lib
 
@@ -132,9 +134,14 @@ def make_stimulus(n_pi: int, *, mean: float, window: int, probs=(0.45, 0.45, 0.0
     tot = lib.synth_stim_counts(*args, _p(counts))
     off = np.zeros(n_pi + 1, np.int64)
     np.cumsum(counts, out=off[1:])
-    t = np.zeros(tot, np.int32)
     v = np.zeros(tot, np.uint8)
-    if lib.synth_stim_fill(*args, _p(off), _p(t), _p(v)) != 0:
+    if window > 2**31 - 1 or n_clock and clock_period * clock_trans > 2**31 - 1:   # 64-bit times
+        t = np.zeros(tot, np.int64)
+        rc = lib.synth_stim_fill64(*args, _p(off), _p(t), _p(v))
+    else:
+        t = np.zeros(tot, np.int32)
+        rc = lib.synth_stim_fill(*args, _p(off), _p(t), _p(v))
+    if rc != 0:
         raise RuntimeError("synth_stim_fill mismatch")
     return Stimulus(off, t, v)
 

@@ -212,7 +212,8 @@ static int draw_value(rng_t *r, const stim_cfg *c, int prev) {
     return (prev + 1) & 3;
 }
 /* one PI waveform; writes at most 'cap' events when t/v non-NULL; returns the count */
-static int64_t gen_pi(const stim_cfg *c, int32_t pi, int32_t *t, uint8_t *v) {
+/* times go to t (32-bit) or t64 (64-bit), whichever is non-null */
+static int64_t gen_pi(const stim_cfg *c, int32_t pi, int32_t *t, int64_t *t64, uint8_t *v) {
     rng_t r; rng_seed(&r, c->seed, 0x5354494Dull + (uint64_t)pi * 0x100000001B3ull);
     int64_t n = 0;
     if (is_clock(c, pi)) {
@@ -220,7 +221,9 @@ static int64_t gen_pi(const stim_cfg *c, int32_t pi, int32_t *t, uint8_t *v) {
         int val = (int)(rng_next(&r) >> 63);
         int64_t half = c->clock_period / 2;
         for (int64_t j = 0; j < c->clock_trans; j++) {
-            if (t) { t[n] = (int32_t)(phase + half * j); v[n] = (uint8_t)val; }
+            if (t) t[n] = (int32_t)(phase + half * j);
+            if (t64) t64[n] = phase + half * j;
+            if (v) v[n] = (uint8_t)val;
             n++; val ^= 1;
         }
         return n;
@@ -233,7 +236,9 @@ static int64_t gen_pi(const stim_cfg *c, int32_t pi, int32_t *t, uint8_t *v) {
         int64_t ti = (int64_t)floor(tc);
         if (ti == last) continue;
         int val = draw_value(&r, c, prev);
-        if (t) { t[n] = (int32_t)ti; v[n] = (uint8_t)val; }
+        if (t) t[n] = (int32_t)ti;
+        if (t64) t64[n] = ti;
+        if (v) v[n] = (uint8_t)val;
         n++; last = ti; prev = val;
     }
     return n;
@@ -263,8 +268,20 @@ int64_t synth_stim_counts(int32_t n_pi, uint64_t seed, double mean, int64_t wind
                           int32_t n_clock, int32_t clock_period, int32_t clock_trans, int64_t *counts) {
     stim_cfg c; make_cfg(&c, n_pi, seed, mean, window, p0, p1, px, pz, n_clock, clock_period, clock_trans);
     int64_t tot = 0;
-    for (int32_t i = 0; i < n_pi; i++) { counts[i] = gen_pi(&c, i, NULL, NULL); tot += counts[i]; }
+    for (int32_t i = 0; i < n_pi; i++) { counts[i] = gen_pi(&c, i, NULL, NULL, NULL); tot += counts[i]; }
     return tot;
+}
+/* synth_stim_fill64: the same transitions with 64-bit times (windows past 2^31 ps) */
+int synth_stim_fill64(int32_t n_pi, uint64_t seed, double mean, int64_t window,
+                      double p0, double p1, double px, double pz,
+                      int32_t n_clock, int32_t clock_period, int32_t clock_trans,
+                      const int64_t *off, int64_t *t, uint8_t *v) {
+    stim_cfg c; make_cfg(&c, n_pi, seed, mean, window, p0, p1, px, pz, n_clock, clock_period, clock_trans);
+    for (int32_t i = 0; i < n_pi; i++) {
+        int64_t n = gen_pi(&c, i, NULL, t + off[i], v + off[i]);
+        if (n != off[i + 1] - off[i]) return -1;
+    }
+    return 0;
 }
 /* synth_stim_fill: the transitions themselves, PI i at [off[i], off[i+1]) */
 int synth_stim_fill(int32_t n_pi, uint64_t seed, double mean, int64_t window,
@@ -273,7 +290,7 @@ int synth_stim_fill(int32_t n_pi, uint64_t seed, double mean, int64_t window,
                     const int64_t *off, int32_t *t, uint8_t *v) {
     stim_cfg c; make_cfg(&c, n_pi, seed, mean, window, p0, p1, px, pz, n_clock, clock_period, clock_trans);
     for (int32_t i = 0; i < n_pi; i++) {
-        int64_t n = gen_pi(&c, i, t + off[i], v + off[i]);
+        int64_t n = gen_pi(&c, i, t + off[i], NULL, v + off[i]);
         if (n != off[i + 1] - off[i]) return -1;
     }
     return 0;
