@@ -24,6 +24,14 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                          64-bit throughout).
   sim_event              same pins as sim_levelized.
   static_eval            hand-computed settle values of small circuits.
+  edge_class             the Verilog posedge/negedge classes, listed by hand
+                         (tests/golden/edge_classes.txt).
+  cell_candidates /      with edge-independent delays and built-in tables,
+  sim_cells              equal to gate_candidates / sim_event (pinned above)
+                         on random netlists; several outputs equal separate
+                         single-output cells; hand-worked edge-dependent XOR
+                         example (tests/golden/edge_delay_xor.txt); a no-arc
+                         entry never wins the minimum.
 """
 from __future__ import annotations
 
@@ -96,6 +104,14 @@ def _load():
         lib.oracle_static_eval.argtypes = [i32, i32, P, P, P, P, P]
         lib.oracle_check_gates.restype = i64
         lib.oracle_check_gates.argtypes = net_args + [P, P, P, i32, i32, ctypes.c_int, ctypes.POINTER(i64)]
+        lib.oracle_edge_class.restype = ctypes.c_int
+        lib.oracle_edge_class.argtypes = [ctypes.c_int, ctypes.c_int]
+        lib.oracle_arc_delay4.restype = i64
+        lib.oracle_arc_delay4.argtypes = [P, ctypes.c_int, ctypes.c_int]
+        lib.oracle_cell_candidates.restype = i64
+        lib.oracle_cell_candidates.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P]
+        lib.oracle_sim_cells.restype = ctypes.c_int
+        lib.oracle_sim_cells.argtypes = [i32, i32, P, P, P, P, P, P, P, P, P, P, ctypes.POINTER(P)]
         _lib = lib
     return _lib
 
@@ -204,6 +220,59 @@ def _result(h) -> Result:
 
 class OracleError(RuntimeError):
     pass
+
+
+# ---- cells with the full delay matrix, several outputs, user tables ----
+EDGE_RISE, EDGE_FALL, EDGE_NONE = 0, 1, 2
+INF = np.iinfo(np.int64).max
+
+
+def edge_class(old: int, new: int) -> int:
+    """0 rising, 1 falling, 2 neither (X<->Z), -1 no change."""
+    return _load().oracle_edge_class(old, new)
+
+
+def arc_delay4(D4, edge: int, v: int) -> int:
+    """Delay of one pin's transition of class `edge` toward output value v;
+    D4[edge * 2 + value], -1 = no arc; INF when no arc applies."""
+    d = _c(D4, np.int64)
+    return _load().oracle_arc_delay4(_p(d), edge, v)
+
+
+def cell_candidates(lut, D, ins):
+    """Algorithm 2 candidates of one cell output: lut = 4^n_in table, D =
+    [n_in][edge][value] delays (-1 = no arc), ins = [(t, v), ...]."""
+    n_in = len(ins)
+    ts, vs, tp, vp, n = _pin_arrays(ins)
+    lut = _c(lut, np.uint8)
+    D = _c(np.asarray(D).reshape(-1), np.int64)
+    cap = int(n.sum()) + 1
+    td, tr, cv = np.zeros(cap, np.int64), np.zeros(cap, np.int64), np.zeros(cap, np.uint8)
+    m = _load().oracle_cell_candidates(n_in, _p(lut), _p(D), ctypes.cast(tp, P), ctypes.cast(vp, P), _p(n),
+                                       _p(td), _p(tr), _p(cv))
+    if m < 0:
+        raise OracleError("an output without any arc")
+    return td[:m], tr[:m], cv[:m]
+
+
+def eval_cell_output(lut, D, ins):
+    """One output waveform of a general cell (Algorithm 2 + Eq. 1)."""
+    td, tr, cv = cell_candidates(lut, D, ins)
+    return cancel_stack(td, tr, cv)
+
+
+def sim_cells(cn, st) -> Result:
+    """Whole netlist of general cells (synth.CellNetlist): nets are the PIs
+    then every cell's outputs in cell order."""
+    so, stt, sv = _c(st.off, np.int64), _c(st.t, np.int64), _c(st.v, np.uint8)
+    h = P()
+    rc = _load().oracle_sim_cells(int(cn.n_pi), len(cn.n_out), _p(_c(cn.n_out, np.int32)), _p(_c(cn.luts, np.uint8)),
+                                  _p(_c(cn.lut_off, np.int64)), _p(_c(cn.fanin_off, np.int32)),
+                                  _p(_c(cn.fanin_net, np.int32)), _p(_c(cn.delays, np.int64)),
+                                  _p(_c(cn.delay_off, np.int64)), _p(so), _p(stt), _p(sv), ctypes.byref(h))
+    if rc:
+        raise OracleError(f"oracle_sim_cells: {rc}")
+    return _result(h)
 
 
 def sim_levelized(nl, st, nthreads: int = 1) -> Result:

@@ -658,3 +658,205 @@ int64_t oracle_check_gates(int32_t n_pi, int32_t G, const uint8_t *type, const i
     *first_bad = (first == INT64_MAX) ? -1 : first;
     return bad;
 }
+
+/* ------------------------------------------------------------------ */
+/* Cells with the full delay matrix, several outputs and user tables   */
+/*
+ * Sec. 3 ("Delay") keeps delays in a five-dimensional matrix indexed by
+ * cell, input pin, output pin, edge of the input transition and value of
+ * the output transition, an entry without an arc being infinite; for an
+ * output k that changes at t, Algorithm 2 takes the minimum of
+ * Delay[i][k][e_i][o_k] over the inputs.  Sec. 3 ("Module Function") builds
+ * every cell, user-defined primitives included, from a logic function per
+ * output.  Here a cell has n_in inputs (1..3) and n_out outputs; output o
+ * has a 4-value table lut[o][sum v_p 4^p] with values 0, 1, X, and delays
+ * D[p][o][edge][value] (edge 0 = rising, 1 = falling; value 0 = the output
+ * falls to 0, 1 = it rises to 1), -1 where pin p has no arc to output o.
+ *
+ * Readings (the paper leaves these open):
+ *   - the edge of an input transition follows Verilog's posedge / negedge
+ *     classes: rising = 0->1, 0->X, 0->Z, X->1, Z->1; falling = 1->0, 1->X,
+ *     1->Z, X->0, Z->0; X<->Z is neither and takes the smaller delay of the
+ *     two edges;
+ *   - an output changing to X takes the smaller of its value-0 and value-1
+ *     delays (as the rise/fall arcs above);
+ *   - as above, only pins with a transition at t enter the minimum, and the
+ *     output is X before its first transition whatever the table gives for
+ *     all-X inputs (Algorithm 2 starts the outputs unknown);
+ *   - when none of the pins that changed at t has an arc to the output (a
+ *     user table can change value through a pin without an arc, e.g. from
+ *     the initial X), the output takes the smallest delay of all its arcs
+ *     toward the new value;
+ *   - the outputs of one cell are scheduled and cancelled (Eq. 1) each on
+ *     its own, since Algorithm 2 keeps one output waveform per output pin.
+ */
+#define EDGE_RISE 0
+#define EDGE_FALL 1
+#define EDGE_NONE 2
+
+int oracle_edge_class(int old, int nw) {
+    if (old == nw) return -1;
+    if (nw == 1 || old == 0) return EDGE_RISE;   /* to 1, or up from 0 */
+    if (nw == 0 || old == 1) return EDGE_FALL;   /* to 0, or down from 1 */
+    return EDGE_NONE;                            /* X <-> Z */
+}
+
+/* Delay of one pin's transition of class `edge` toward output value v;
+   D4 = that pin's [edge][value] entries for the output, -1 = no arc. */
+int64_t oracle_arc_delay4(const int64_t *D4, int edge, int v) {
+    int64_t d = INF64;
+    for (int e = 0; e < 2; e++) {
+        if (edge != EDGE_NONE && e != edge) continue;
+        for (int val = 0; val < 2; val++) {
+            if (v != VX && val != v) continue;
+            int64_t x = D4[2 * e + val];
+            if (x >= 0 && x < d) d = x;
+        }
+    }
+    return d;
+}
+
+/*
+ * Algorithm 2 for one output of a cell: lut = that output's 4^n_in table,
+ * D = the output's delays, D[p * 4 + edge * 2 + value].  Candidates as in
+ * oracle_gate_candidates; returns the count, or -1 if the output has no arc
+ * at all.
+ */
+int64_t oracle_cell_candidates(int n_in, const uint8_t *lut, const int64_t *D, const int64_t *const *in_t,
+                               const uint8_t *const *in_v, const int64_t *in_n, int64_t *cd_td, int64_t *cd_tr,
+                               uint8_t *cd_v) {
+    uint8_t cur[3] = {VX, VX, VX};
+    int64_t idx[3] = {0, 0, 0}, n = 0;
+    int F = VX;                                   /* the output before any input event */
+    for (;;) {
+        int64_t t = INF64;
+        for (int p = 0; p < n_in; p++)
+            if (idx[p] < in_n[p] && in_t[p][idx[p]] < t) t = in_t[p][idx[p]];
+        if (t == INF64) break;
+        int edge[3] = {-1, -1, -1};
+        for (int p = 0; p < n_in; p++) {
+            if (idx[p] < in_n[p] && in_t[p][idx[p]] == t) {
+                uint8_t nv = in_v[p][idx[p]];
+                edge[p] = oracle_edge_class(cur[p], nv);
+                cur[p] = nv;
+                idx[p]++;
+            }
+        }
+        int li = 0;
+        for (int p = n_in - 1; p >= 0; p--) li = li * 4 + cur[p];
+        int nF = lut[li];
+        if (nF != F) {
+            int64_t d = INF64;
+            for (int p = 0; p < n_in; p++) {
+                if (edge[p] < 0) continue;
+                int64_t dp = oracle_arc_delay4(D + 4 * p, edge[p], nF);
+                if (dp < d) d = dp;
+            }
+            if (d == INF64)   /* no changed pin has an arc: the fastest arc of the output */
+                for (int p = 0; p < n_in; p++) {
+                    int64_t dp = oracle_arc_delay4(D + 4 * p, EDGE_NONE, nF);
+                    if (dp < d) d = dp;
+                }
+            if (d == INF64) return -1;
+            cd_td[n] = t; cd_tr[n] = t + d; cd_v[n] = (uint8_t)nF; n++;
+        }
+        F = nF;
+    }
+    return n;
+}
+
+/*
+ * Whole netlist of such cells, evaluated cell by cell once all fanin nets
+ * are known (Kahn order).  Nets: 0..n_pi-1 primary inputs, then the outputs
+ * of cell 0, cell 1, ... in order.  Cell c: inputs fanin_net[fanin_off[c]..
+ * fanin_off[c+1]) (n_in = that count), n_out[c] outputs, tables at
+ * luts[lut_off[c] + o * 4^n_in], delays at delays[delay_off[c] +
+ * ((p * n_out + o) * 2 + edge) * 2 + value].  Returns 0, -1 for a bad
+ * netlist, -2 for a cycle, -3 for a changed output without a finite delay,
+ * -5 when out of memory.
+ */
+int oracle_sim_cells(int32_t n_pi, int32_t n_cells, const int32_t *n_out, const uint8_t *luts,
+                     const int64_t *lut_off, const int32_t *fanin_off, const int32_t *fanin_net,
+                     const int64_t *delays, const int64_t *delay_off, const int64_t *soff, const int64_t *st,
+                     const uint8_t *sv, oracle_result **out) {
+    *out = NULL;
+    int64_t *obase = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_cells + 1));
+    if (!obase) return -5;
+    obase[0] = n_pi;
+    for (int32_t c = 0; c < n_cells; c++) {
+        int k = fanin_off[c + 1] - fanin_off[c];
+        if (k < 1 || k > 3 || n_out[c] < 1) { free(obase); return -1; }
+        obase[c + 1] = obase[c] + n_out[c];
+    }
+    const int64_t N = obase[n_cells];
+    int32_t *owner = (int32_t *)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));  /* net -> cell, -1 = PI */
+    int32_t *need = (int32_t *)calloc((size_t)(n_cells > 0 ? n_cells : 1), sizeof(int32_t));
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_cells > 0 ? n_cells : 1));
+    wave_t *w = (wave_t *)calloc((size_t)(N > 0 ? N : 1), sizeof(wave_t));
+    if (!owner || !need || !queue || !w) return -5;
+    for (int64_t q = 0; q < n_pi; q++) owner[q] = -1;
+    for (int32_t c = 0; c < n_cells; c++)
+        for (int64_t q = obase[c]; q < obase[c + 1]; q++) owner[q] = c;
+    /* readers of each cell, for Kahn's algorithm */
+    int64_t *roff = (int64_t *)calloc((size_t)n_cells + 1, sizeof(int64_t));
+    int32_t *rd = (int32_t *)malloc(sizeof(int32_t) * (size_t)(fanin_off[n_cells] > 0 ? fanin_off[n_cells] : 1));
+    for (int32_t c = 0; c < n_cells; c++)
+        for (int32_t a = fanin_off[c]; a < fanin_off[c + 1]; a++) {
+            int32_t net = fanin_net[a];
+            if (net < 0 || net >= N) { free(obase); return -1; }
+            if (owner[net] >= 0) { roff[owner[net] + 1]++; need[c]++; }
+        }
+    for (int32_t c = 0; c < n_cells; c++) roff[c + 1] += roff[c];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_cells + 1));
+    memcpy(fill, roff, sizeof(int64_t) * (size_t)(n_cells + 1));
+    for (int32_t c = 0; c < n_cells; c++)
+        for (int32_t a = fanin_off[c]; a < fanin_off[c + 1]; a++)
+            if (owner[fanin_net[a]] >= 0) rd[fill[owner[fanin_net[a]]]++] = c;
+    load_pis(w, n_pi, soff, st, sv);
+    int32_t head = 0, tail = 0;
+    for (int32_t c = 0; c < n_cells; c++) if (need[c] == 0) queue[tail++] = c;
+    int rc = 0;
+    int64_t cap = 0, *td = NULL, *tr = NULL, *ot = NULL; uint8_t *cv = NULL, *ov = NULL;
+    while (head < tail && rc == 0) {
+        int32_t c = queue[head++];
+        int k = fanin_off[c + 1] - fanin_off[c];
+        const int64_t *it[3]; const uint8_t *iv[3]; int64_t in_n[3], tot = 0;
+        for (int p = 0; p < k; p++) {
+            wave_t *src = &w[fanin_net[fanin_off[c] + p]];
+            it[p] = src->t; iv[p] = src->v; in_n[p] = src->n; tot += src->n;
+        }
+        if (tot + 1 > cap) {
+            cap = (tot + 1) * 2;
+            td = (int64_t *)realloc(td, sizeof(int64_t) * (size_t)cap);
+            tr = (int64_t *)realloc(tr, sizeof(int64_t) * (size_t)cap);
+            ot = (int64_t *)realloc(ot, sizeof(int64_t) * (size_t)cap);
+            cv = (uint8_t *)realloc(cv, (size_t)cap);
+            ov = (uint8_t *)realloc(ov, (size_t)cap);
+        }
+        const int nl = 1 << (2 * k);
+        for (int o = 0; o < n_out[c]; o++) {
+            int64_t D[12];
+            for (int p = 0; p < k; p++)
+                for (int j = 0; j < 4; j++) D[4 * p + j] = delays[delay_off[c] + ((int64_t)p * n_out[c] + o) * 4 + j];
+            int64_t nc = oracle_cell_candidates(k, luts + lut_off[c] + (int64_t)o * nl, D, it, iv, in_n, td, tr, cv);
+            if (nc < 0) { rc = -3; break; }
+            int64_t m = oracle_cancel_stack(nc, td, tr, cv, ot, ov);
+            wave_t *dst = &w[obase[c] + o];
+            dst->t = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+            dst->v = (uint8_t *)malloc((size_t)(m > 0 ? m : 1));
+            if (!dst->t || !dst->v) { rc = -5; break; }
+            memcpy(dst->t, ot, sizeof(int64_t) * (size_t)m);
+            memcpy(dst->v, ov, (size_t)m);
+            dst->n = dst->cap = m;
+        }
+        for (int64_t s = roff[c]; s < roff[c + 1]; s++)
+            if (--need[rd[s]] == 0) queue[tail++] = rd[s];
+    }
+    if (rc == 0 && tail != n_cells) rc = -2;
+    free(td); free(tr); free(ot); free(cv); free(ov);
+    free(obase); free(owner); free(need); free(queue); free(roff); free(rd); free(fill);
+    if (rc) { free_waves(w, N); return rc; }
+    *out = assemble(w, N);
+    free_waves(w, N);
+    return *out ? 0 : -5;
+}

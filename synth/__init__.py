@@ -147,6 +147,109 @@ def make_stimulus(n_pi: int, *, mean: float, window: int, probs=(0.45, 0.45, 0.0
 
 
 @dataclass
+class CellNetlist:
+    """Netlist of general cells: cell c reads nets fanin_net[fanin_off[c]:
+    fanin_off[c+1]] (n_in = that count, 1..3) and drives n_out[c] nets.  Nets
+    0..n_pi-1 are primary inputs, then the outputs of cell 0, cell 1, ... in
+    order.  Output o of cell c has the 4-value table luts[lut_off[c] + o *
+    4^n_in + sum v_p 4^p] (0, 1, 2 = X) and delays delays[delay_off[c] +
+    ((p * n_out + o) * 2 + edge) * 2 + value] (edge 0 rising, 1 falling;
+    value 0 = falling to 0, 1 = rising to 1; -1 = no arc from pin p)."""
+    n_pi: int
+    n_out: np.ndarray       # int32[C]
+    fanin_off: np.ndarray   # int32[C+1]
+    fanin_net: np.ndarray   # int32[A]
+    luts: np.ndarray        # uint8
+    lut_off: np.ndarray     # int64[C+1]
+    delays: np.ndarray      # int32
+    delay_off: np.ndarray   # int64[C+1]
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.n_out.shape[0])
+
+    @property
+    def n_nets(self) -> int:
+        return int(self.n_pi + self.n_out.sum())
+
+    def n_in(self, c: int) -> int:
+        return int(self.fanin_off[c + 1] - self.fanin_off[c])
+
+
+def make_cell_netlist(n_pi: int, n_cells: int, depth: int, *, seed: int = 1, multi_frac: float = 0.3,
+                      edge_frac: float = 0.5, noarc_frac: float = 0.1, x_frac: float = 0.6, d_min: int = 5,
+                      d_max: int = 200, fanout: str = "pareto", shuffle: bool = False) -> CellNetlist:
+    """Seeded general-cell netlist on the structure of make_netlist: each cell
+    has 1 or 2 outputs (multi_frac), user tables drawn at random (0/1 inputs
+    give a random 0/1; inputs with X/Z give X with probability x_frac, else a
+    random 0/1), delays uniform in [d_min, d_max] that depend on the input
+    edge for a fraction edge_frac of the outputs, and, for a fraction
+    noarc_frac of (pin, output) pairs of multi-input cells, no arc -- the
+    output's table is then made independent of that pin.  About half of the
+    reads of a 2-output cell use its second output."""
+    base = make_netlist(n_pi, n_cells, depth, fanout=fanout, d_min=d_min, d_max=d_max, seed=seed, shuffle=shuffle)
+    rng = np.random.default_rng(seed * 7919 + 17)
+    C = base.n_gates
+    k = np.diff(base.fanin_off).astype(np.int64)
+    n_out = np.where(rng.random(C) < multi_frac, 2, 1).astype(np.int32)
+    obase = np.zeros(C + 1, np.int64)
+    obase[0] = n_pi
+    np.cumsum(n_out, out=obase[1:])
+    obase[1:] += n_pi
+    # rewire reads: gate g's net -> one of cell g's outputs
+    net = base.fanin_net.astype(np.int64)
+    g = net - n_pi
+    isg = g >= 0
+    gg = np.where(isg, g, 0)
+    second = isg & (n_out[gg] == 2) & (rng.random(len(net)) < 0.5)
+    fanin_net = np.where(isg, obase[gg] + second, net).astype(np.int32)
+    nl4 = 4 ** k
+    lut_off = np.zeros(C + 1, np.int64)
+    np.cumsum(n_out * nl4, out=lut_off[1:])
+    delay_off = np.zeros(C + 1, np.int64)
+    np.cumsum(k * n_out * 4, out=delay_off[1:])
+    luts = np.zeros(int(lut_off[-1]), np.uint8)
+    delays = np.zeros(int(delay_off[-1]), np.int32)
+    for kk in (1, 2, 3):
+        cells = np.nonzero(k == kk)[0]
+        if len(cells) == 0:
+            continue
+        n4 = 4 ** kk
+        idx = np.arange(n4)
+        digits = np.stack([(idx >> (2 * p)) & 3 for p in range(kk)])          # [kk, n4]
+        all01 = np.all(digits <= 1, axis=0)
+        for o in (0, 1):
+            cs = cells[n_out[cells] > o]
+            if len(cs) == 0:
+                continue
+            T = rng.integers(0, 2, (len(cs), n4)).astype(np.uint8)
+            xs = (rng.random((len(cs), n4)) < x_frac) & ~all01
+            T[xs] = 2
+            D = rng.integers(d_min, d_max + 1, (len(cs), kk, 2, 2)).astype(np.int32)
+            same = rng.random(len(cs)) >= edge_frac
+            D[same, :, 1, :] = D[same, :, 0, :]
+            if kk > 1:
+                noarc = rng.random((len(cs), kk)) < noarc_frac
+                noarc[noarc.all(axis=1), 0] = False          # keep at least one arc
+                for p in range(kk):
+                    rows = np.nonzero(noarc[:, p])[0]
+                    if len(rows) == 0:
+                        continue
+                    src = idx & ~(3 << (2 * p))                  # the same entry with pin p at 0
+                    T[rows] = T[rows][:, src]
+                    D[rows, p] = -1
+            base_l = lut_off[cs] + o * n4
+            luts[(base_l[:, None] + idx[None, :]).reshape(-1)] = T.reshape(-1)
+            # delays[delay_off + ((p * n_out + o) * 2 + e) * 2 + v]
+            for p in range(kk):
+                for e in (0, 1):
+                    for v in (0, 1):
+                        at = delay_off[cs] + ((p * n_out[cs] + o) * 2 + e) * 2 + v
+                        delays[at] = D[:, p, e, v]
+    return CellNetlist(n_pi, n_out, base.fanin_off.astype(np.int32), fanin_net, luts, lut_off, delays, delay_off)
+
+
+@dataclass
 class Workload:
     name: str
     netlist: Netlist
