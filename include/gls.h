@@ -247,6 +247,56 @@ int gls_read_waveform(gls_ctx *ctx, int32_t run_id, int32_t net, int32_t *t, uin
 int gls_read_all(gls_ctx *ctx, int32_t run_id, int64_t *off, uint32_t *packed, int64_t cap);
 
 /*
+ * ---- General cells: full delay matrix, several outputs, user tables -------
+ *
+ * Sec. 3 keeps delays in a five-dimensional matrix [cell][input pin][output
+ * pin][input edge][output value], an entry without an arc being infinite,
+ * and builds every cell, user-defined primitives (UDP) included, from one
+ * logic function per output.  A netlist of general cells: cell c reads
+ * fanin_net[fanin_off[c]..fanin_off[c+1]) (pins a, b, c in order) and drives
+ * one net per output; nets are numbered 0..n_pi-1 for the primary inputs,
+ * then the outputs of cell 0, cell 1, ... in order.  delays holds, cell after
+ * cell, n_in * n_out * 4 entries: delays[((p * n_out + o) * 2 + edge) * 2 +
+ * value] with edge 0 for a rising and 1 for a falling input transition and
+ * value 0 when the output falls to 0, 1 when it rises to 1, in ps; all four
+ * entries of (p, o) are -1 when pin p has no arc to output o, else in
+ * [1, 2^29).
+ * Semantics (in addition to gls_simulate's): the edge of an input transition
+ * follows Verilog's posedge/negedge classes (rising: 0->1, 0->X, 0->Z, X->1,
+ * Z->1; falling: the mirror images); an X<->Z transition takes the smaller
+ * delay of both edges; an output changing to X the smaller of both values;
+ * an output whose change involves no pin with an arc takes its fastest arc
+ * toward the new value; an output is X before its first transition
+ * whatever its table gives for all-X inputs; each output is scheduled and
+ * cancelled (Eq. 1) on its own.
+ */
+#define GLS_USER_CELL_BASE 16    /* first cell type id of gls_define_cell */
+#define GLS_MAX_CELL_OUTPUTS 8
+
+/* The 4^k-entry table of built-in cell `cell` (entry sum v_p 4^p over its k
+   pins, values 0, 1, 2 = X), as the library evaluates it: the common value
+   of the Boolean function over every 0/1 completion of X/Z inputs. */
+int gls_cell_table(int32_t cell, uint8_t *table);
+
+/* Define a cell (a UDP or a multi-output library cell) for this context:
+   n_inputs in 1..3, n_outputs in 1..GLS_MAX_CELL_OUTPUTS, tables[o * 4^n_inputs
+   + sum v_p 4^p] in {0, 1, 2 = X} for inputs v_p in {0, 1, 2 = X, 3 = Z}.
+   *cell_type = GLS_USER_CELL_BASE + (cells defined before).  GLS_EINVAL for
+   bad sizes or values. */
+int gls_define_cell(gls_ctx *ctx, int32_t n_inputs, int32_t n_outputs, const uint8_t *tables,
+                    int32_t *cell_type);
+
+/* Load a netlist of general cells (built-in ids 0..GLS_NCELLS-1 with one
+   output, or gls_define_cell ids); layout and delays as described above.
+   The same checks and errors as gls_load_netlist, plus GLS_EINVAL for an
+   output without any arc.  Netlists with edge-dependent delays, pins without
+   arcs or an output that is not X for all-X inputs run on the windowed
+   kernels only (GLS_EINVAL at run creation with GLS_KERNEL_SEGMENTED). */
+int gls_load_netlist_cells(gls_ctx *ctx, int32_t n_pi, int32_t n_cells, const int32_t *cell_type,
+                           const int32_t *fanin_off, const int32_t *fanin_net, const int32_t *delays,
+                           int32_t *netlist_id);
+
+/*
  * ---- Task division over time and 64-bit times ----------------------------
  *
  * A stimulus may run longer than the 2^30 - 1 ps a device transition holds

@@ -105,31 +105,72 @@ struct Levelized {
     int64_t max_path_delay = 0;
 };
 
-int analyse_netlist(int32_t n_pi, int32_t G, const uint8_t *type, const int32_t *fanin_off, const int32_t *fanin_net,
-                    const int32_t *d_rise, const int32_t *d_fall, Levelized *out) {
+// Per-arc delays of the general form: d4[a * 4 + edge * 2 + value] (edge 0
+// rising, 1 falling; value 0 the output falls, 1 it rises); all four -1 for
+// a pin without an arc.
+int check_arcs(int32_t n_pi, int32_t G, const int32_t *fanin_off, const int32_t *fanin_net, const int32_t *d4) {
+    if (n_pi < 0 || G < 0) return fail(GLS_EINVAL, "negative n_pi or n_gates");
+    if (G > 0 && (!fanin_off || !fanin_net || !d4)) return fail(GLS_EINVAL, "NULL netlist array");
+    if ((int64_t)n_pi + G >= (int64_t)INT32_MAX) return fail(GLS_EINVAL, "too many nets");
+    const int64_t N = (int64_t)n_pi + G;
+    if (G > 0 && fanin_off[0] != 0) return fail(GLS_EINVAL, "fanin_off[0] must be 0");
+    for (int32_t g = 0; g < G; g++) {
+        const int32_t k = fanin_off[g + 1] - fanin_off[g];
+        if (k < 1 || k > 3) return fail(GLS_EINVAL, "gate %d: %d input pins (1..3 supported)", g, k);
+        int32_t lo = INT32_MAX, hi = 0, arcs = 0;
+        for (int32_t a = fanin_off[g]; a < fanin_off[g + 1]; a++) {
+            if (fanin_net[a] < 0 || fanin_net[a] >= N) return fail(GLS_EINVAL, "gate %d: net %d out of range", g, fanin_net[a]);
+            if (fanin_net[a] == n_pi + g) return fail(GLS_ECYCLE, "gate %d reads its own output", g);
+            const int32_t *d = d4 + 4 * (int64_t)a;
+            const bool none = d[0] == -1 && d[1] == -1 && d[2] == -1 && d[3] == -1;
+            if (none) continue;
+            arcs++;
+            for (int j = 0; j < 4; j++) {
+                if (d[j] < 1 || d[j] >= kMaxDelay)
+                    return fail(GLS_EINVAL, "gate %d pin %d: delay %d out of [1, 2^29) (all four -1 = no arc)", g,
+                                a - fanin_off[g], d[j]);
+                lo = std::min(lo, d[j]);
+                hi = std::max(hi, d[j]);
+            }
+        }
+        if (arcs == 0) return fail(GLS_EINVAL, "gate %d: no pin has an arc to the output", g);
+        if (hi - lo > GLS_MAX_DELAY_SPREAD)
+            return fail(GLS_ERANGE, "gate %d: delay spread %d exceeds %d", g, hi - lo, GLS_MAX_DELAY_SPREAD);
+    }
+    return GLS_OK;
+}
+
+// The classic form -- a built-in cell per gate, rise/fall per arc for both
+// input edges -- checked and put in the general per-arc layout.
+int classic_arcs(int32_t n_pi, int32_t G, const uint8_t *type, const int32_t *fanin_off, const int32_t *fanin_net,
+                 const int32_t *d_rise, const int32_t *d_fall, std::vector<int32_t> &d4) {
     if (n_pi < 0 || G < 0) return fail(GLS_EINVAL, "negative n_pi or n_gates");
     if (G > 0 && (!type || !fanin_off || !fanin_net || !d_rise || !d_fall))
         return fail(GLS_EINVAL, "NULL netlist array");
-    if ((int64_t)n_pi + G >= (int64_t)INT32_MAX) return fail(GLS_EINVAL, "too many nets");
-    const int64_t N = (int64_t)n_pi + G;
     if (G > 0 && fanin_off[0] != 0) return fail(GLS_EINVAL, "fanin_off[0] must be 0");
     for (int32_t g = 0; g < G; g++) {
         if (type[g] >= GLS_NCELLS) return fail(GLS_EINVAL, "gate %d: unknown cell %d", g, type[g]);
         if (fanin_off[g + 1] - fanin_off[g] != kArity[type[g]])
             return fail(GLS_EINVAL, "gate %d: %d fanins for a %d-pin cell", g, fanin_off[g + 1] - fanin_off[g],
                         kArity[type[g]]);
-        int32_t lo = INT32_MAX, hi = 0;
-        for (int32_t a = fanin_off[g]; a < fanin_off[g + 1]; a++) {
-            if (fanin_net[a] < 0 || fanin_net[a] >= N) return fail(GLS_EINVAL, "gate %d: net %d out of range", g, fanin_net[a]);
-            if (fanin_net[a] == n_pi + g) return fail(GLS_ECYCLE, "gate %d reads its own output", g);
+        for (int32_t a = fanin_off[g]; a < fanin_off[g + 1]; a++)
             if (d_rise[a] < 1 || d_fall[a] < 1 || d_rise[a] >= kMaxDelay || d_fall[a] >= kMaxDelay)
                 return fail(GLS_EINVAL, "gate %d: delay out of [1, 2^29)", g);
-            lo = std::min(lo, std::min(d_rise[a], d_fall[a]));
-            hi = std::max(hi, std::max(d_rise[a], d_fall[a]));
-        }
-        if (hi - lo > GLS_MAX_DELAY_SPREAD)
-            return fail(GLS_ERANGE, "gate %d: delay spread %d exceeds %d", g, hi - lo, GLS_MAX_DELAY_SPREAD);
     }
+    const int64_t A = G > 0 ? fanin_off[G] : 0;
+    d4.resize((size_t)std::max<int64_t>(4 * A, 4));
+    for (int64_t a = 0; a < A; a++) {
+        d4[4 * a + 0] = d4[4 * a + 2] = d_fall[a];
+        d4[4 * a + 1] = d4[4 * a + 3] = d_rise[a];
+    }
+    return GLS_OK;
+}
+
+// Levels, level order and the longest path delay of a checked netlist.
+int analyse_netlist(int32_t n_pi, int32_t G, const int32_t *fanin_off, const int32_t *fanin_net, const int32_t *d4,
+                    Levelized *out) {
+    int rc = check_arcs(n_pi, G, fanin_off, fanin_net, d4);
+    if (rc) return rc;
     // Kahn's algorithm over gate->gate arcs; level = 1 + max fanin level
     std::vector<int32_t> need(G, 0), level(G, 1), fo_cnt(G + 1, 0);
     for (int32_t g = 0; g < G; g++)
@@ -167,7 +208,7 @@ int analyse_netlist(int32_t n_pi, int32_t G, const uint8_t *type, const int32_t 
         out->order[p] = g;
         out->pos[g] = p;
     }
-    // longest path delay (max over arcs of the larger of rise/fall)
+    // longest path delay (max over arcs of the largest entry)
     std::vector<int64_t> pd(G, 0);
     int64_t best = 0;
     for (int32_t p = 0; p < G; p++) {
@@ -175,7 +216,8 @@ int analyse_netlist(int32_t n_pi, int32_t G, const uint8_t *type, const int32_t 
         int64_t m = 0;
         for (int32_t a = fanin_off[g]; a < fanin_off[g + 1]; a++) {
             int64_t in = fanin_net[a] >= n_pi ? pd[fanin_net[a] - n_pi] : 0;
-            m = std::max(m, in + std::max(d_rise[a], d_fall[a]));
+            const int32_t *d = d4 + 4 * (int64_t)a;
+            m = std::max(m, in + std::max(std::max(d[0], d[1]), std::max(d[2], d[3])));
         }
         pd[g] = m;
         best = std::max(best, m);
@@ -231,8 +273,14 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+struct UserCell {
+    int32_t n_in = 0, n_out = 0;
+    std::vector<uint8_t> tables;       // n_out tables of 4^n_in values
+};
+
 struct NetlistObj {
     int32_t n_pi = 0, n_gates = 0;
+    bool general = false;              // a record needs the windowed kernels (kGateGeneral)
     Levelized lv;
     GateRec *d_gates = nullptr;
     int32_t *d_ext2int = nullptr;      // [N] caller net id -> internal net id
@@ -322,6 +370,7 @@ struct gls_ctx {
     std::map<uint64_t, uint64_t> pool_free;           // offset -> size of free ranges
     std::unordered_map<void *, uint64_t> pool_allocs; // block -> size
     uint32_t *d_status = nullptr;       // scratch for stimulus packing (3 words)
+    std::vector<UserCell> cells;        // gls_define_cell, type GLS_USER_CELL_BASE + index
 };
 
 namespace {
@@ -568,6 +617,9 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
         if (!n) return fail(GLS_EINVAL, "item %d: unknown netlist id %d", i, netlist_ids[i]);
         if (!s) return fail(GLS_EINVAL, "item %d: unknown stimulus id %d", i, stim_ids[i]);
         if (s->n_pi != n->n_pi) return fail(GLS_EINVAL, "item %d: stimulus has %d PIs, netlist %d", i, s->n_pi, n->n_pi);
+        if (n->general && c->cfg.variant == kVariantSegmented)
+            return fail(GLS_EINVAL, "item %d: the netlist has edge-dependent delays, pins without arcs or a cell that "
+                        "is not X for all-X inputs; these run on the windowed kernels", i);
         if (slice_ps > 0) {
             // slice-local times: inputs below slice_ps, outputs below slice_ps + the longest path
             if (slice_ps + n->lv.max_path_delay >= (int64_t)kTimeLimit)
@@ -787,7 +839,9 @@ int gls_check_netlist(int32_t n_pi, int32_t n_gates, const uint8_t *type, const 
                       int32_t *level_out) {
     try {
         Levelized lv;
-        int rc = analyse_netlist(n_pi, n_gates, type, fanin_off, fanin_net, d_rise, d_fall, &lv);
+        std::vector<int32_t> d4;
+        int rc = classic_arcs(n_pi, n_gates, type, fanin_off, fanin_net, d_rise, d_fall, d4);
+        if (!rc) rc = analyse_netlist(n_pi, n_gates, fanin_off, fanin_net, d4.data(), &lv);
         if (rc) return rc;
         if (depth_out) *depth_out = lv.depth;
         if (level_out) std::copy(lv.level.begin(), lv.level.end(), level_out);
@@ -817,9 +871,6 @@ int gls_create(gls_ctx **out, int device, uint64_t hbm_budget_bytes) {
         CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
         CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-        uint64_t lut[GLS_NCELLS][2];
-        build_luts(lut);
-        set_luts(lut, GLS_NCELLS);
         CK(cudaGetLastError());
         int rc = apply_launch_cfg(c.get(), kVariantWindowed, 4);
         if (rc) return rc;
@@ -848,13 +899,16 @@ void gls_destroy(gls_ctx *c) {
 
 const char *gls_last_error(gls_ctx *) { return g_err.c_str(); }
 
-int gls_load_netlist(gls_ctx *c, int32_t n_pi, int32_t n_gates, const uint8_t *type, const int32_t *fanin_off,
-                     const int32_t *fanin_net, const int32_t *d_rise, const int32_t *d_fall, int32_t *netlist_id) {
-    if (!c || !netlist_id) return fail(GLS_EINVAL, "NULL argument");
+// A netlist in the general form: gate g (one cell output) reads
+// fanin_net[fanin_off[g]..fanin_off[g+1]] with per-arc delays d4 (see
+// check_arcs), its function is the 64-entry table lut[g] and types[g] is
+// its built-in cell id (255 for user cells).
+static int load_general(gls_ctx *c, int32_t n_pi, int32_t n_gates, const int32_t *fanin_off, const int32_t *fanin_net,
+                        const int32_t *d4, const uint64_t (*lut)[2], const uint8_t *types, int32_t *netlist_id) {
     try {
         CK(cudaSetDevice(c->device));
         auto n = std::make_unique<NetlistObj>();
-        int rc = analyse_netlist(n_pi, n_gates, type, fanin_off, fanin_net, d_rise, d_fall, &n->lv);
+        int rc = analyse_netlist(n_pi, n_gates, fanin_off, fanin_net, d4, &n->lv);
         if (rc) return rc;
         n->n_pi = n_pi;
         n->n_gates = n_gates;
@@ -864,18 +918,32 @@ int gls_load_netlist(gls_ctx *c, int32_t n_pi, int32_t n_gates, const uint8_t *t
             const int32_t g = n->lv.order[p];
             GateRec &r = recs[p];
             std::memset(&r, 0, sizeof r);
-            r.type = type[g];
-            r.k = (uint8_t)kArity[type[g]];
+            r.lut_lo = lut[g][0];
+            r.lut_hi = lut[g][1];
+            r.type = types[g];
+            r.k = (uint8_t)(fanin_off[g + 1] - fanin_off[g]);
             r.out_net = (uint32_t)(n_pi + p);
             int32_t dmin = INT32_MAX;
             for (int q = 0; q < r.k; q++) {
-                const int32_t a = fanin_off[g] + q, net = fanin_net[a];
-                r.fin[q] = net < n_pi ? net : n_pi + n->lv.pos[net - n_pi];
-                r.rise[q] = d_rise[a];
-                r.fall[q] = d_fall[a];
-                dmin = std::min(dmin, std::min(d_rise[a], d_fall[a]));
+                const int32_t *d = d4 + 4 * ((int64_t)fanin_off[g] + q);
+                if (d[0] >= 0) for (int j = 0; j < 4; j++) dmin = std::min(dmin, d[j]);
             }
             r.dmin = dmin;
+            bool edge = false;
+            for (int q = 0; q < r.k; q++) {
+                const int32_t a = fanin_off[g] + q, net = fanin_net[a];
+                r.fin[q] = net < n_pi ? net : n_pi + n->lv.pos[net - n_pi];
+                const int32_t *d = d4 + 4 * (int64_t)a;
+                const bool arc = d[0] >= 0;
+                if (arc) r.arcs |= (uint8_t)(1u << q);
+                for (int e = 0; e < 2; e++)
+                    for (int v = 0; v < 2; v++) r.doff[q][e][v] = arc ? (uint8_t)(d[e * 2 + v] - dmin) : kNoArc;
+                edge |= arc && (d[0] != d[2] || d[1] != d[3]);
+            }
+            const bool all_x_is_x = ((r.lut_hi >> (2 * (42 - 32))) & 3u) == 2u;   // inputs X, X, X
+            if (edge) r.flags |= kGateEdge;
+            if (edge || r.arcs != (uint8_t)((1u << r.k) - 1) || !all_x_is_x) r.flags |= kGateGeneral;
+            if (r.flags & kGateGeneral) n->general = true;
         }
         n->ext2int.resize(N);
         for (int32_t i = 0; i < n_pi; i++) n->ext2int[i] = i;
@@ -895,6 +963,118 @@ int gls_load_netlist(gls_ctx *c, int32_t n_pi, int32_t n_gates, const uint8_t *t
         c->netlists[id] = std::move(n);
         *netlist_id = id;
         return GLS_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(GLS_ENOMEM, "host allocation failed");
+    }
+}
+
+int gls_load_netlist(gls_ctx *c, int32_t n_pi, int32_t n_gates, const uint8_t *type, const int32_t *fanin_off,
+                     const int32_t *fanin_net, const int32_t *d_rise, const int32_t *d_fall, int32_t *netlist_id) {
+    if (!c || !netlist_id) return fail(GLS_EINVAL, "NULL argument");
+    try {
+        std::vector<int32_t> d4;
+        int rc = classic_arcs(n_pi, n_gates, type, fanin_off, fanin_net, d_rise, d_fall, d4);
+        if (rc) return rc;
+        uint64_t bl[GLS_NCELLS][2];
+        build_luts(bl);
+        std::vector<uint64_t> lut(2 * (size_t)std::max(n_gates, 1));
+        for (int32_t g = 0; g < n_gates; g++) {
+            lut[2 * (size_t)g] = bl[type[g]][0];
+            lut[2 * (size_t)g + 1] = bl[type[g]][1];
+        }
+        return load_general(c, n_pi, n_gates, fanin_off, fanin_net, d4.data(),
+                            reinterpret_cast<const uint64_t (*)[2]>(lut.data()), type, netlist_id);
+    } catch (const std::bad_alloc &) {
+        return fail(GLS_ENOMEM, "host allocation failed");
+    }
+}
+
+int gls_cell_table(int32_t cell, uint8_t *table) {
+    if (cell < 0 || cell >= GLS_NCELLS || !table) return fail(GLS_EINVAL, "built-in cell id %d", cell);
+    uint64_t bl[GLS_NCELLS][2];
+    build_luts(bl);
+    const int k = kArity[cell];
+    for (int i = 0; i < (1 << (2 * k)); i++) {
+        // pins beyond k read X in the 64-entry table
+        int idx = i;
+        for (int p = k; p < 3; p++) idx |= 2 << (2 * p);
+        table[i] = (uint8_t)((bl[cell][idx >> 5] >> (2 * (idx & 31))) & 3u);
+    }
+    return GLS_OK;
+}
+
+int gls_define_cell(gls_ctx *c, int32_t n_inputs, int32_t n_outputs, const uint8_t *tables, int32_t *cell_type) {
+    if (!c || !tables || !cell_type) return fail(GLS_EINVAL, "NULL argument");
+    if (n_inputs < 1 || n_inputs > 3) return fail(GLS_EINVAL, "%d inputs (1..3 supported)", n_inputs);
+    if (n_outputs < 1 || n_outputs > GLS_MAX_CELL_OUTPUTS)
+        return fail(GLS_EINVAL, "%d outputs (1..%d supported)", n_outputs, GLS_MAX_CELL_OUTPUTS);
+    const int n4 = 1 << (2 * n_inputs);
+    for (int i = 0; i < n_outputs * n4; i++)
+        if (tables[i] > 2) return fail(GLS_EINVAL, "table entry %d: value %d (0, 1 or 2 = X)", i, tables[i]);
+    try {
+        UserCell u;
+        u.n_in = n_inputs;
+        u.n_out = n_outputs;
+        u.tables.assign(tables, tables + (size_t)n_outputs * n4);
+        c->cells.push_back(std::move(u));
+        *cell_type = GLS_USER_CELL_BASE + (int32_t)c->cells.size() - 1;
+        return GLS_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(GLS_ENOMEM, "host allocation failed");
+    }
+}
+
+int gls_load_netlist_cells(gls_ctx *c, int32_t n_pi, int32_t n_cells, const int32_t *cell_type,
+                           const int32_t *fanin_off, const int32_t *fanin_net, const int32_t *delays,
+                           int32_t *netlist_id) {
+    if (!c || !netlist_id) return fail(GLS_EINVAL, "NULL argument");
+    if (n_pi < 0 || n_cells < 0) return fail(GLS_EINVAL, "negative n_pi or n_cells");
+    if (n_cells > 0 && (!cell_type || !fanin_off || !fanin_net || !delays)) return fail(GLS_EINVAL, "NULL netlist array");
+    if (n_cells > 0 && fanin_off[0] != 0) return fail(GLS_EINVAL, "fanin_off[0] must be 0");
+    try {
+        uint64_t bl[GLS_NCELLS][2];
+        build_luts(bl);
+        // every cell output becomes one gate; its nets keep the caller's numbering
+        std::vector<int32_t> goff(1, 0), gnet, d4;
+        std::vector<uint64_t> lut;
+        std::vector<uint8_t> types;
+        int64_t dpos = 0;
+        for (int32_t cc = 0; cc < n_cells; cc++) {
+            const int32_t T = cell_type[cc];
+            int n_in, n_out;
+            const UserCell *u = nullptr;
+            if (T >= 0 && T < GLS_NCELLS) { n_in = kArity[T]; n_out = 1; }
+            else if (T >= GLS_USER_CELL_BASE && T - GLS_USER_CELL_BASE < (int32_t)c->cells.size()) {
+                u = &c->cells[T - GLS_USER_CELL_BASE];
+                n_in = u->n_in;
+                n_out = u->n_out;
+            } else return fail(GLS_EINVAL, "cell %d: unknown cell type %d", cc, T);
+            if (fanin_off[cc + 1] - fanin_off[cc] != n_in)
+                return fail(GLS_EINVAL, "cell %d: %d fanins for a %d-input cell", cc, fanin_off[cc + 1] - fanin_off[cc], n_in);
+            const int n4 = 1 << (2 * n_in);
+            for (int o = 0; o < n_out; o++) {
+                for (int p = 0; p < n_in; p++) {
+                    gnet.push_back(fanin_net[fanin_off[cc] + p]);
+                    for (int j = 0; j < 4; j++) d4.push_back(delays[dpos + ((int64_t)p * n_out + o) * 4 + j]);
+                }
+                goff.push_back((int32_t)gnet.size());
+                uint64_t w[2] = {0, 0};
+                for (int idx = 0; idx < 64; idx++) {
+                    const int i = idx & (n4 - 1);   // the cell's own pins; the others read X in the kernel
+                    const uint64_t v = u ? u->tables[(size_t)o * n4 + i] : ((bl[T][idx >> 5] >> (2 * (idx & 31))) & 3u);
+                    w[idx >> 5] |= v << (2 * (idx & 31));
+                }
+                lut.push_back(w[0]);
+                lut.push_back(w[1]);
+                types.push_back(u ? (uint8_t)255 : (uint8_t)T);
+            }
+            dpos += (int64_t)n_in * n_out * 4;
+        }
+        const int64_t G = (int64_t)types.size();
+        if ((int64_t)n_pi + G >= (int64_t)INT32_MAX) return fail(GLS_EINVAL, "too many nets");
+        if (G == 0) { d4.assign(4, 0); lut.assign(2, 0); types.assign(1, 0); }
+        return load_general(c, n_pi, (int32_t)G, goff.data(), gnet.data(), d4.data(),
+                            reinterpret_cast<const uint64_t (*)[2]>(lut.data()), types.data(), netlist_id);
     } catch (const std::bad_alloc &) {
         return fail(GLS_ENOMEM, "host allocation failed");
     }
@@ -1311,6 +1491,9 @@ int gls_simulate_noalloc(gls_ctx *c, int32_t netlist_id, int32_t stim_id, uint64
     if (!n) return fail(GLS_EINVAL, "unknown netlist id %d", netlist_id);
     if (!s) return fail(GLS_EINVAL, "unknown stimulus id %d", stim_id);
     if (s->n_pi != n->n_pi) return fail(GLS_EINVAL, "stimulus has %d PIs, netlist %d", s->n_pi, n->n_pi);
+    if (s->wide) return fail(GLS_EINVAL, "a stimulus with 64-bit times runs only in time slices");
+    if (n->general && c->cfg.variant == kVariantSegmented)
+        return fail(GLS_EINVAL, "the netlist needs the windowed kernels");
     if (n->lv.depth > GLS_NOALLOC_MAX_LEVELS)
         return fail(GLS_ERANGE, "netlist depth %d exceeds the %d levels of the no-allocation scratch",
                     n->lv.depth, GLS_NOALLOC_MAX_LEVELS);

@@ -42,12 +42,6 @@
 
 namespace gls {
 
-__constant__ uint64_t c_lut[16][2];
-
-void set_luts(const uint64_t lut[][2], int ncells) {
-    cudaMemcpyToSymbol(c_lut, lut, sizeof(uint64_t) * 2 * ncells);
-}
-
 namespace {
 
 constexpr int PCAP = kPendCap;          // carried (pending) transitions, > GLS_MAX_DELAY_SPREAD
@@ -67,6 +61,10 @@ struct __align__(16) WarpSmem {
     // walk: B (2 CH + 4 words, sentinel-terminated) and Binfo (source of B[i]:
     // pin b flag (bit 15) | index in its window; 2 CH + 8 halves).
     uint32_t Q[PCAP + 3 * CH + 8];
+    // cells whose delays depend on the input edge: delay - dmin by output
+    // value (0, 1, X) and set of (pin, edge) pairs changed at the timestamp
+    // (bit 2p: pin p rose, bit 2p+1: it fell; both for X<->Z)
+    uint8_t dtab[3][64];
     __device__ __forceinline__ uint32_t *B() { return Q + PCAP; }
     __device__ __forceinline__ uint16_t *Binfo() { return reinterpret_cast<uint16_t *>(Q + PCAP + 2 * CH + 4); }
 };
@@ -118,7 +116,7 @@ __device__ __forceinline__ uint32_t setpin(uint32_t st, int pin, uint32_t v) {
 struct GateCtx {
     const uint32_t *src[3];
     uint32_t len[3];
-    uint32_t rise[3], fall[3], dx[3];
+    uint32_t rise[3], fall[3], dx[3];   // pin 0's arc (one-input cells)
     uint32_t dmin, dmax;
     uint64_t lut_lo, lut_hi;
     // min over the pins of a pin set of (delay - dmin), one byte per set
@@ -128,8 +126,9 @@ struct GateCtx {
 };
 
 // Delay of a timestamp at which the pins of set `grp` changed and the cell's
-// value became F (min over those pins, Sec. 3 delay rule).  Byte grp of the
-// table pair; the other bytes of the permute read byte 0, which is 0.
+// value became F (min over those pins with an arc, Sec. 3 delay rule; the
+// output's fastest arc when none has one).  Byte grp of the table pair; the
+// other bytes of the permute read byte 0, which is 0.
 template <int K>
 __device__ __forceinline__ uint32_t group_delay(const GateCtx &g, uint32_t F, uint32_t grp) {
     const uint32_t lo = F == 1u ? g.dr_lo : (F == 0u ? g.df_lo : g.dx_lo);
@@ -139,6 +138,14 @@ __device__ __forceinline__ uint32_t group_delay(const GateCtx &g, uint32_t F, ui
 
 __device__ __forceinline__ uint32_t pin_delay(const GateCtx &g, int p, uint32_t F) {
     return F == 1u ? g.rise[p] : (F == 0u ? g.fall[p] : g.dx[p]);
+}
+
+// Edge class of a pin transition old -> new, index old * 4 + new, 2 bits
+// each: 1 rising (0->1, 0->X, 0->Z, X->1, Z->1), 2 falling (the mirror
+// images), 3 neither (X<->Z, counted as both edges).
+constexpr uint32_t kEdgeLut = 0x36C6A254u;
+__device__ __forceinline__ uint32_t edge_class(uint32_t old, uint32_t nw) {
+    return (kEdgeLut >> (2u * ((old << 2) | nw))) & 3u;
 }
 
 // Issue the asynchronous copies of every pin's next window into buffer b.
@@ -235,7 +242,7 @@ __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0,
     return true;
 }
 
-template <int K, bool DEP, int CH>
+template <int K, bool DEP, int CH, bool EDGE>
 __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane) {
     GateCtx g;
     uint64_t bound = 0;
@@ -254,34 +261,65 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
             }
             g.src[p] = reinterpret_cast<const uint32_t *>(ptr);
             g.len[p] = len;
-            g.rise[p] = (uint32_t)gr.rise[p];
-            g.fall[p] = (uint32_t)gr.fall[p];
-            g.dx[p] = min(g.rise[p], g.fall[p]);
         } else {
             g.src[p] = nullptr;
             g.len[p] = 0;
-            g.rise[p] = g.fall[p] = g.dx[p] = 0;
         }
         bound += g.len[p];
     }
     g.dmin = (uint32_t)gr.dmin;
-    g.lut_lo = c_lut[gr.type][0];
-    g.lut_hi = c_lut[gr.type][1];
-    g.dmax = 0;
+    g.lut_lo = gr.lut_lo;
+    g.lut_hi = gr.lut_hi;
+    // delay tables from the record's [pin][edge][value] offsets
+    const uint32_t arcs = gr.arcs;
+    uint32_t fb_f = 255u, fb_r = 255u, omax = 0;   // fastest arcs to 0 / to 1, slowest arc
+#pragma unroll
+    for (int p = 0; p < K; p++)
+        if ((arcs >> p) & 1u)
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                fb_f = min(fb_f, (uint32_t)gr.doff[p][e][0]);
+                fb_r = min(fb_r, (uint32_t)gr.doff[p][e][1]);
+                omax = max(omax, max((uint32_t)gr.doff[p][e][0], (uint32_t)gr.doff[p][e][1]));
+            }
+    g.dmax = g.dmin + omax;
+    g.rise[0] = g.dmin + gr.doff[0][0][1];
+    g.fall[0] = g.dmin + gr.doff[0][0][0];
+    g.dx[0] = min(g.rise[0], g.fall[0]);
     g.df_lo = g.df_hi = g.dr_lo = g.dr_hi = 0;
+    if (!EDGE) {
 #pragma unroll
-    for (int set = 1; set < 8; set++) {
-        uint32_t f = 255u, rr = 255u;   // sets with a pin >= K never occur
+        for (int set = 1; set < 8; set++) {
+            uint32_t f = 255u, rr = 255u;   // sets with a pin >= K never occur
+            const uint32_t in = (uint32_t)set & arcs;
 #pragma unroll
-        for (int p = 0; p < K; p++)
-            if ((set >> p) & 1) { f = min(f, g.fall[p] - g.dmin); rr = min(rr, g.rise[p] - g.dmin); }
-        if (set < 4) { g.df_lo |= f << (8 * set); g.dr_lo |= rr << (8 * set); }
-        else { g.df_hi |= f << (8 * (set - 4)); g.dr_hi |= rr << (8 * (set - 4)); }
+            for (int p = 0; p < K; p++)
+                if ((in >> p) & 1u) { f = min(f, (uint32_t)gr.doff[p][0][0]); rr = min(rr, (uint32_t)gr.doff[p][0][1]); }
+            if (in == 0) { f = fb_f; rr = fb_r; }
+            if (set < 4) { g.df_lo |= f << (8 * set); g.dr_lo |= rr << (8 * set); }
+            else { g.df_hi |= f << (8 * (set - 4)); g.dr_hi |= rr << (8 * (set - 4)); }
+        }
+        g.dx_lo = __vminu4(g.df_lo, g.dr_lo);
+        g.dx_hi = __vminu4(g.df_hi, g.dr_hi);
+    } else {
+        for (int x = lane; x < 192; x += 32) {
+            const int F = x >> 6, vm = x & 63;
+            uint32_t d = 255u;
+            bool any = false;
+#pragma unroll
+            for (int p = 0; p < K; p++)
+#pragma unroll
+                for (int e = 0; e < 2; e++)
+                    if (((vm >> (2 * p + e)) & 1) && ((arcs >> p) & 1u)) {
+                        const uint32_t d0 = gr.doff[p][e][0], d1 = gr.doff[p][e][1];
+                        d = min(d, F == 0 ? d0 : (F == 1 ? d1 : min(d0, d1)));
+                        any = true;
+                    }
+            if (!any) d = F == 0 ? fb_f : (F == 1 ? fb_r : min(fb_f, fb_r));
+            sm.dtab[F][vm] = (uint8_t)d;
+        }
+        __syncwarp();
     }
-    g.dx_lo = __vminu4(g.df_lo, g.dr_lo);
-    g.dx_hi = __vminu4(g.df_hi, g.dr_hi);
-#pragma unroll
-    for (int p = 0; p < K; p++) g.dmax = max(g.dmax, max(g.rise[p], g.fall[p]));
     const uint32_t out_net = gr.out_net;
 
     // state before the first input transition: pins at X, output X, nothing
@@ -289,9 +327,11 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
     uint32_t carry = 0x2Au;
     CommitState cs{0u, kVX, 0};
     uint32_t send = kTimeInf;   // transitions with t_r >= send stay pending
+    bool started = false;       // an input transition was evaluated (else the output is still at its X start)
     if (r.st_in) {
         const uint32_t h = r.st_in[out_net];
         carry = (h & 63u) ^ 0x2Au;
+        started = (h >> 7) & 1u;
         cs.lastV = ((h >> 8) & 3u) ^ kVX;
         cs.np = (int)(h >> 16);
         bound += (uint64_t)cs.np;   // each carried transition may become an output
@@ -417,13 +457,22 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         // inside the lane's share) and kept by advancing the top.
         if (K == 1) {
             // one pin: every transition is its own timestamp
-            uint32_t Fprev = (lut1 >> (2 * (d0 > 0 ? (L[d0 - 1] & 3u) : (carry & 3u)))) & 3u;
+            uint32_t vprev = d0 > 0 ? (L[d0 - 1] & 3u) : (carry & 3u);   // pin value before the share
+            // the output before the first input transition is X (Algorithm 2)
+            uint32_t Fprev = (d0 == 0 && !started) ? kVX : (lut1 >> (2 * vprev)) & 3u;
             uint32_t topv = 0;   // cand[top - 1] when top > d0
             for (int s = d0; s < d1; s++) {
                 const uint32_t e = L[s], t = e >> 2;
                 const uint32_t F = (lut1 >> (2 * (e & 3u))) & 3u;
                 const bool chg = F != Fprev;
-                const uint32_t key = (t + pin_delay(g, 0, F)) << 2;
+                uint32_t dl;
+                if (EDGE) {
+                    dl = g.dmin + sm.dtab[F][edge_class(vprev, e & 3u)];
+                    vprev = e & 3u;
+                } else {
+                    dl = pin_delay(g, 0, F);
+                }
+                const uint32_t key = (t + dl) << 2;
                 while (chg && top > d0 && topv >= key) {
                     top--;
                     topv = top > d0 ? sm.cand[top - 1] : 0u;
@@ -459,21 +508,28 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
             uint32_t hl = L[i], hr = R[j];
             uint32_t hinfo = K == 3 ? sm.Binfo()[i] : 0u;   // source of the L head (3-pin cells)
             uint32_t Fprev = 0;
-            uint32_t grp = 0;   // pins with a transition at the current timestamp
+            // pins with a transition at the current timestamp: one bit per pin,
+            // or, for edge-dependent delays, the (pin, edge) bits of dtab
+            uint32_t grp = 0;
             if (d0 < d1) {
                 // cell value just before the first timestamp of this share, and
                 // the pins whose transitions at that timestamp precede the share
                 const uint32_t tf = min(hl, hr) >> 2;
                 uint32_t sb = st;
+                int npre = 0;   // transitions at tf before the share
 #pragma unroll
                 for (int p = 0; p < K; p++)
                     if (cc[p] > 0 && ltp[p] == tf) {
                         const uint32_t v = cc[p] >= 2 ? (A[p][cc[p] - 2] & 3u) : ((carry >> (2 * p)) & 3u);
                         sb = setpin(sb, p, v);
-                        grp |= 1u << p;
+                        grp |= EDGE ? edge_class(v, A[p][cc[p] - 1] & 3u) << (2 * p) : 1u << p;
+                        npre++;
                     }
                 Fprev = K == 3 ? (uint32_t)(((sb & 32u) ? g.lut_hi : g.lut_lo) >> (2 * (sb & 31u))) & 3u
                                : (lut2 >> (2 * (sb & 15u))) & 3u;
+                // tf is the gate's first timestamp: the output is still at its X
+                // start (Algorithm 2), whatever the table gives for X inputs
+                if (!started && d0 == npre) Fprev = kVX;
             }
             bool gend = false;   // the previous transition closed its timestamp
             uint32_t topv = 0;   // cand[top - 1] when top > d0
@@ -487,13 +543,16 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
                 hr = tl ? hr : y;
                 if (K == 3) hinfo = sm.Binfo()[i];
                 const uint32_t t = e >> 2;
+                uint32_t bit;
+                if (EDGE) bit = edge_class((st >> (2 * pin)) & 3u, e & 3u) << (2 * pin);
+                else bit = 1u << pin;
                 st = setpin(st, (int)pin, e & 3u);
-                grp = (gend ? 0u : grp) | (1u << pin);
+                grp = (gend ? 0u : grp) | bit;
                 const bool end = (min(hl, hr) >> 2) != t;   // last transition at this time
                 const uint32_t F = K == 3 ? (uint32_t)(((st & 32u) ? g.lut_hi : g.lut_lo) >> (2 * (st & 31u))) & 3u
                                           : (lut2 >> (2 * (st & 15u))) & 3u;
                 const bool chg = end && F != Fprev;
-                const uint32_t key = (t + group_delay<K>(g, F, grp)) << 2;
+                const uint32_t key = (t + (EDGE ? g.dmin + sm.dtab[F][grp] : group_delay<K>(g, F, grp))) << 2;
                 while (chg && top > d0 && topv >= key) {
                     top--;
                     topv = top > d0 ? sm.cand[top - 1] : 0u;
@@ -512,6 +571,7 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
 #pragma unroll
         for (int p = 0; p < K; p++)
             if (m[p] > 0) carry = setpin(carry, p, A[p][m[p] - 1] & 3u);
+        started = true;
 #pragma unroll
         for (int p = 0; p < 3; p++) { cur[p] = ncur[p]; lead[p] = nlead[p]; n[p] = nn[p]; }
         b ^= 1;
@@ -522,7 +582,9 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         // no input transition in this slice: settle the carried ones alone
         if (!any_input) failed = !commit_chunk<CH>(sm, lane, 0, 0, send, out, cs);
         if (!failed) {
-            if (lane == 0) r.st_out[out_net] = (carry ^ 0x2Au) | ((cs.lastV ^ kVX) << 8) | ((uint32_t)cs.np << 16);
+            if (lane == 0)
+                r.st_out[out_net] = (carry ^ 0x2Au) | ((uint32_t)(started || any_input) << 7) | ((cs.lastV ^ kVX) << 8) |
+                                    ((uint32_t)cs.np << 16);
             uint32_t *pp = r.pend_out + (size_t)out_net * PCAP;
             for (int x = lane; x < cs.np; x += 32) pp[x] = sm.Q[x];
         }
@@ -536,10 +598,18 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
 
 template <bool DEP, int CH>
 __device__ __forceinline__ void eval_windowed(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane) {
+    if (gr.flags & kGateEdge) {
+        switch (gr.k) {
+        case 1: eval_gate<1, DEP, CH, true>(gr, r, sm, lane); break;
+        case 2: eval_gate<2, DEP, CH, true>(gr, r, sm, lane); break;
+        default: eval_gate<3, DEP, CH, true>(gr, r, sm, lane); break;
+        }
+        return;
+    }
     switch (gr.k) {
-    case 1: eval_gate<1, DEP, CH>(gr, r, sm, lane); break;
-    case 2: eval_gate<2, DEP, CH>(gr, r, sm, lane); break;
-    default: eval_gate<3, DEP, CH>(gr, r, sm, lane); break;
+    case 1: eval_gate<1, DEP, CH, false>(gr, r, sm, lane); break;
+    case 2: eval_gate<2, DEP, CH, false>(gr, r, sm, lane); break;
+    default: eval_gate<3, DEP, CH, false>(gr, r, sm, lane); break;
     }
 }
 
@@ -650,8 +720,8 @@ __device__ void eval_gate_seg(const GateRec &gr, const RunDev &r, int lane) {
             len[p] = __ldg(r.net_len + n);
         }
         src[p] = reinterpret_cast<const uint32_t *>(ptr);
-        rise[p] = (uint32_t)gr.rise[p];
-        fall[p] = (uint32_t)gr.fall[p];
+        rise[p] = (uint32_t)gr.dmin + gr.doff[p][0][1];
+        fall[p] = (uint32_t)gr.dmin + gr.doff[p][0][0];
         bound += len[p];
     }
     const uint32_t out_net = gr.out_net;
@@ -671,7 +741,7 @@ __device__ void eval_gate_seg(const GateRec &gr, const RunDev &r, int lane) {
         return;
     }
     uint32_t *const slot = r.arena + base;
-    const uint64_t lut_lo = c_lut[gr.type][0], lut_hi = c_lut[gr.type][1];
+    const uint64_t lut_lo = gr.lut_lo, lut_hi = gr.lut_hi;
 
     // ---- segments: lane l takes input times [T_l, T_l+1) ----
     const uint32_t S = (uint32_t)min((uint64_t)32, (bound + r.seg_target - 1) / r.seg_target);

@@ -13,17 +13,34 @@ constexpr uint32_t kVX = 2;
 constexpr uint32_t kTimeLimit = (1u << 30) - 1u;   // exclusive
 constexpr uint32_t kTimeInf = 0xFFFFFFFFu;         // "no more transitions"
 
-// Device gate record, gates stored in level order (48 bytes, 16-byte aligned).
-// fin[] are internal net ids: 0..n_pi-1 primary inputs, n_pi+i internal gate i.
+// Device gate record: one output of one cell, records in level order (64
+// bytes, 16-byte aligned).  fin[] are internal net ids: 0..n_pi-1 primary
+// inputs, n_pi+i the output of record i.
+//   lut      the output's 4-value function over pins a, b, c: entry
+//            sum v_p 4^p (2 bits: 0, 1, X) of lut_lo (entries 0..31) and
+//            lut_hi (32..63); the pins a cell does not have read X
+//   doff     delay - dmin by [pin][input edge (0 rising, 1 falling)]
+//            [output value (0 falls, 1 rises)]; kNoArc where the pin has no
+//            arc to this output
+//   flags    kGateEdge: the delays depend on the input edge;
+//            kGateGeneral: the record needs the windowed kernels (edge
+//            delays, a pin without an arc, or an output that is not X for
+//            all-X inputs)
 struct __align__(16) GateRec {
+    uint64_t lut_lo, lut_hi;
     int32_t fin[3];
-    int32_t rise[3];
-    int32_t fall[3];
-    int32_t dmin;        // min over the arcs of min(rise, fall)
+    int32_t dmin;        // smallest delay over the arcs
     uint32_t out_net;    // internal net id of the output (n_pi + i)
-    uint8_t type, k, pad0, pad1;
+    uint8_t doff[3][2][2];
+    uint8_t type;        // built-in cell id, or 255 for a user-defined cell
+    uint8_t k;           // input pins
+    uint8_t flags;
+    uint8_t arcs;        // bit p: pin p has an arc to this output
+    uint32_t pad[2];
 };
-static_assert(sizeof(GateRec) == 48, "GateRec layout");
+static_assert(sizeof(GateRec) == 64, "GateRec layout");
+constexpr uint8_t kNoArc = 255;
+enum : uint8_t { kGateEdge = 1, kGateGeneral = 2 };
 
 // Status bits a run's kernels may raise.
 enum : uint32_t {
@@ -59,10 +76,11 @@ struct RunDev {
     int32_t planned;
     // Time-sliced runs (task division over time), else null: every gate's
     // state at the start (st_in, pend_in) and end (st_out, pend_out) of the
-    // slice, per net.  st = (input pins ^ 0x2A) | (output value ^ X) << 8 |
-    // pending count << 16, so all-zero is the start state (inputs X, output
-    // X, nothing pending); pend holds kPendCap pending transitions per net in
-    // the previous slice's local time.
+    // slice, per net.  st = (input pins ^ 0x2A) | started << 7 | (output
+    // value ^ X) << 8 | pending count << 16, so all-zero is the start state
+    // (inputs X, no input transition yet, output X, nothing pending); pend
+    // holds kPendCap pending transitions per net in the previous slice's
+    // local time.
     uint32_t *st_in, *st_out, *pend_in, *pend_out;
     uint32_t slice_end;       // local end of the slice: a t_r at or past it stays pending
     uint32_t slice_shift;     // start of this slice minus start of the previous one
@@ -102,7 +120,6 @@ __host__ __device__ inline uint64_t stim_words(int64_t n_events, int64_t n_pi) {
 }
 
 // ---- launch wrappers ----
-void set_luts(const uint64_t lut[][2], int ncells);
 size_t gate_smem_bytes(int variant, int warps_per_cta);
 int gate_max_ctas_per_sm(int variant, int warps_per_cta);
 // one level: gates [g_begin, g_begin + g_count) of the level-ordered array

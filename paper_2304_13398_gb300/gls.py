@@ -46,6 +46,9 @@ SIGNATURES = [
     ("gls_run_query", ctypes.c_int, [P, i32]),
     ("gls_run_info", ctypes.c_int, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     ("gls_plan_order", ctypes.c_int, [P, i32, i32, i32]),
+    ("gls_cell_table", ctypes.c_int, [i32, P]),
+    ("gls_define_cell", ctypes.c_int, [P, i32, i32, P, ctypes.POINTER(i32)]),
+    ("gls_load_netlist_cells", ctypes.c_int, [P, i32, i32, P, P, P, P, ctypes.POINTER(i32)]),
     ("gls_load_stimulus64", ctypes.c_int, [P, i32, P, P, P, ctypes.POINTER(i32)]),
     ("gls_simulate_sliced", ctypes.c_int, [P, i32, i32, i64, i64, P, ctypes.POINTER(i32)]),
     ("gls_run_slices", ctypes.c_int, [P, i32, ctypes.POINTER(i32)]),
@@ -203,6 +206,40 @@ class Context:
         n_pi = len(off) - 1 if n_pi is None else n_pi
         self._ck(self.lib.gls_load_stimulus(self.h, n_pi, _p(off), _p(t), _p(v), ctypes.byref(sid)))
         return sid.value
+
+    def define_cell(self, n_inputs: int, tables) -> int:
+        """A user cell (UDP / multi-output cell): tables = n_outputs x 4^n_inputs
+        values in {0, 1, 2 = X}.  Returns its cell type id."""
+        t = _c(tables, np.uint8)
+        n4 = 4 ** n_inputs
+        if t.size % n4:
+            raise ValueError("tables must hold n_outputs * 4^n_inputs values")
+        ct = ctypes.c_int32(0)
+        self._ck(self.lib.gls_define_cell(self.h, n_inputs, t.size // n4, _p(t), ctypes.byref(ct)))
+        self.__dict__.setdefault("_outs", {})[ct.value] = t.size // n4
+        return ct.value
+
+    def load_netlist_cells(self, n_pi: int, cell_type, fanin_off, fanin_net, delays) -> int:
+        """A netlist of general cells (see include/gls.h)."""
+        ct, fo, fn, d = (_c(cell_type, np.int32), _c(fanin_off, np.int32), _c(fanin_net, np.int32),
+                         _c(delays, np.int32))
+        nid = ctypes.c_int32(0)
+        self._ck(self.lib.gls_load_netlist_cells(self.h, n_pi, len(ct), _p(ct), _p(fo), _p(fn), _p(d),
+                                                 ctypes.byref(nid)))
+        self.n_nets[nid.value] = n_pi + self._cell_outputs(ct)
+        return nid.value
+
+    def _cell_outputs(self, ct) -> int:
+        outs = getattr(self, "_outs", {})
+        return int(sum(outs.get(int(x), 1) for x in ct))
+
+    def load_cell_netlist(self, cn) -> int:
+        """Load a CellNetlist whose cells each carry their own tables: one
+        user cell per instance."""
+        types = np.zeros(cn.n_cells, np.int32)
+        for c in range(cn.n_cells):
+            types[c] = self.define_cell(cn.n_in(c), cn.luts[cn.lut_off[c]:cn.lut_off[c + 1]])
+        return self.load_netlist_cells(cn.n_pi, types, cn.fanin_off, cn.fanin_net, cn.delays)
 
     def load_stimulus64(self, st, n_pi: int | None = None) -> int:
         """A stimulus with 64-bit times (for simulate_sliced)."""
@@ -364,6 +401,16 @@ def _ptr(a, dt):
     if hasattr(a, "data_ptr"):
         return P(a.data_ptr())
     raise TypeError(type(a))
+
+
+def cell_table(cell: int) -> np.ndarray:
+    """The library's 4^k table of a built-in cell."""
+    k = int(load_library().gls_cell_arity(cell))
+    out = np.zeros(4 ** k, np.uint8)
+    rc = load_library().gls_cell_table(cell, out.ctypes.data_as(ctypes.c_void_p))
+    if rc != GLS_OK:
+        raise GlsError(rc, "gls_cell_table")
+    return out
 
 
 def unpack(packed: np.ndarray):

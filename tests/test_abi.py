@@ -114,3 +114,13 @@ def test_context_needs_a_gpu(lib):
     rc = lib.gls_create(ctypes.byref(h), 0, 0)
     assert rc in (gls.gls.GLS_ECUDA, gls.gls.GLS_EINVAL)
     assert lib.gls_last_error(None)
+
+
+def test_builtin_cell_tables_equal_oracle():
+    """The library's 4-value tables (Kleene evaluation of prime-implicant
+    covers) against the oracle's (enumeration of 0/1 completions): two
+    independent derivations of the same cell functions, on the host."""
+    import oracle
+    import paper_2304_13398_gb300 as gls
+    for c in range(11):
+        np.testing.assert_array_equal(gls.cell_table(c), oracle.cell_lut(c))
