@@ -75,7 +75,7 @@ def parse():
                     help="dependency schedule: critical-path-first order planned from a calibration run "
                          "(an independent stimulus over 5%% of the window), or plain level order")
     ap.add_argument("--warps-per-cta", type=int, default=0)
-    ap.add_argument("--kernel", default="windowed", choices=["windowed", "wide", "segmented"])
+    ap.add_argument("--kernel", default="wide", choices=["windowed", "wide", "segmented"])
     ap.add_argument("--segment", type=int, default=0, help="segmented kernel: transitions per lane segment")
     return ap.parse_args()
 

@@ -358,7 +358,7 @@ typedef enum gls_option {
     GLS_OPT_TEST_WITHHOLD_GATE = 4, /* test hook for the bounded wait: the gate at this level-order
                                        position never signals completion, so its readers wait out
                                        the limit and the run reports GLS_ETIMEOUT (-1 = off)     */
-    GLS_OPT_KERNEL = 5,         /* GLS_KERNEL_WINDOWED (default) or GLS_KERNEL_SEGMENTED        */
+    GLS_OPT_KERNEL = 5,         /* GLS_KERNEL_WINDOWED_WIDE (default), _WINDOWED or _SEGMENTED  */
     GLS_OPT_SEGMENT = 6,        /* segmented kernel: input transitions per lane segment, >= 1
                                    (default 32); a gate uses min(32, ceil(inputs / this)) lanes */
     GLS_OPT_POOL_BYTES = 7      /* > 0: allocate one device region of this size now and carve

@@ -354,7 +354,7 @@ struct gls_ctx {
     uint64_t budget = 0, used = 0;
     cudaStream_t stream = nullptr, cap_stream = nullptr;
     int sm_count = 0;
-    LevelCfg cfg{4, 0, kVariantWindowed};
+    LevelCfg cfg{4, 0, kVariantWindowedWide};
     int schedule = GLS_SCHEDULE_DEPENDENCY;
     uint64_t wait_limit_ns = 10ull * 1000 * 1000 * 1000;
     int32_t withhold_gate = -1;
@@ -872,7 +872,7 @@ int gls_create(gls_ctx **out, int device, uint64_t hbm_budget_bytes) {
         CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
         CK(cudaGetLastError());
-        int rc = apply_launch_cfg(c.get(), kVariantWindowed, 4);
+        int rc = apply_launch_cfg(c.get(), kVariantWindowedWide, 4);
         if (rc) return rc;
         rc = dalloc_n(c.get(), &c->d_status, 4);
         if (rc) return rc;

@@ -966,7 +966,7 @@ __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin,
 // Completion flags are per net: primary inputs start done, a gate's output
 // net is released once its waveform and descriptor are written.
 template <int V>
-__global__ void __maxnreg__(72) dependency_kernel(const GateRec *__restrict__ gates, int32_t n_gates, int32_t ctr_slot, RunDev r) {
+__global__ void __maxnreg__(V == kVariantWindowed ? 72 : 128) dependency_kernel(const GateRec *__restrict__ gates, int32_t n_gates, int32_t ctr_slot, RunDev r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t L = 1;
