@@ -449,6 +449,7 @@ def run_batch(a):
     r = synth.RECIPES["ind1m"]
     nl = synth.make_netlist(seed=a.seed, **r["net"])
     nid = ctx.load_netlist(nl)
+    order = plan_from_calibration(ctx, nid, nl, r["stim"], a.seed) if a.order == "planned" else "level"
     sids, pi_events = [], []
     for s in range(1, a.batch_sets + 1):
         st = synth.make_stimulus(nl.n_pi, seed=s, **r["stim"])
@@ -522,7 +523,7 @@ def run_batch(a):
             "mode": "batch", "transitions": b_tr, "device_ms": b_ms, "wall_s": b_wall,
             "plain": {"value": p_tr / (p_ms / 1000.0), "unit": UNIT, "device_ms": p_ms, "transitions": p_tr},
             "speedup_vs_plain": (b_tr / b_ms) / (p_tr / p_ms), "items_match_plain": b_tr == p_tr,
-            "wave_size": wave, "waves": waves, "autotune": {"best": tune.best,
+            "gate_order_1m": order, "wave_size": wave, "waves": waves, "autotune": {"best": tune.best,
                                                              "trials": [[c, m] for c, m in tune.timings_ms]},
             "data": "synthetic", "dtype": "u32 packed events"}
     print(json.dumps(line))
@@ -622,8 +623,9 @@ def run_serve(a):
         nl, st, _, stim = make_scaled(int(G), 7000 + i)
         res.append((f"n{i}", nl, st, stim["window"]))
     out = {}
-    for mode, kw in (("served", dict(batching=True, streams=4, max_batch=16)),
-                     ("plain", dict(batching=False, streams=1))):
+    for mode, kw in (("served", dict(batching=True, streams=4, max_batch=16, policy="sjf")),
+                     ("served_fifo", dict(batching=True, streams=4, max_batch=16, policy="fifo")),
+                     ("plain", dict(batching=False, streams=1, policy="fifo"))):
         srv = Server(ctx, budget_bytes=budget, **kw)
         for key, nl, st, window in res:
             srv.add_resident(key, nl, st, window)
@@ -641,7 +643,7 @@ def run_serve(a):
     ctx.close()
     line = {"metric": "served output transitions/s and p50/p99 latency (200 req/s, 8 resident netlists 5k-5M gates)",
             "value": out["served"]["transitions_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
-            "mode": "serve", "served": out["served"], "plain": out["plain"],
+            "mode": "serve", "served": out["served"], "served_fifo": out["served_fifo"], "plain": out["plain"],
             "netlists": [int(x) for x in sizes], "budget_bytes": budget,
             "latency": "request arrival -> its waveforms resident on the device",
             "data": "synthetic", "dtype": "u32 packed events"}

@@ -15,9 +15,10 @@ from dataclasses import dataclass
 from . import gls as _g
 
 DEFAULT_CANDIDATES = [
+    {"kernel": "wide", "warps_per_cta": 4},
+    {"kernel": "wide", "warps_per_cta": 2},
     {"kernel": "windowed", "warps_per_cta": 4},
     {"kernel": "windowed", "warps_per_cta": 2},
-    {"kernel": "wide", "warps_per_cta": 2},
     {"kernel": "segmented", "warps_per_cta": 4, "segment": 32},
     {"kernel": "segmented", "warps_per_cta": 4, "segment": 128},
 ]

@@ -377,8 +377,23 @@ namespace {
 
 // First-fit allocation from the context's pool (no CUDA call, so creating
 // and freeing run buffers never synchronises the device).
-void *pool_take(gls_ctx *c, uint64_t bytes) {
+// Long-lived objects (netlists, stimuli, planned orders) are carved from the
+// top of the pool and runs from the bottom, so releasing a run leaves one
+// large free range instead of gaps between persistent blocks.
+void *pool_take(gls_ctx *c, uint64_t bytes, bool persistent) {
     bytes = (bytes + 255) & ~255ull;
+    if (persistent) {
+        for (auto it = c->pool_free.rbegin(); it != c->pool_free.rend(); ++it) {
+            if (it->second < bytes) continue;
+            const uint64_t off = it->first, size = it->second;
+            if (size > bytes) it->second = size - bytes;
+            else c->pool_free.erase(std::next(it).base());
+            void *p = c->pool + off + size - bytes;
+            c->pool_allocs[p] = bytes;
+            return p;
+        }
+        return nullptr;
+    }
     for (auto it = c->pool_free.begin(); it != c->pool_free.end(); ++it) {
         if (it->second < bytes) continue;
         const uint64_t off = it->first, size = it->second;
@@ -412,11 +427,11 @@ bool pool_give(gls_ctx *c, void *p) {
     return true;
 }
 
-int dalloc(gls_ctx *c, void **p, size_t bytes) {
+int dalloc(gls_ctx *c, void **p, size_t bytes, bool persistent = false) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
     if (c->pool) {
-        *p = pool_take(c, bytes);
+        *p = pool_take(c, bytes, persistent);
         if (!*p)
             return fail(GLS_ENOMEM, "device pool of %llu bytes has no free block of %llu bytes",
                         (unsigned long long)c->pool_bytes, (unsigned long long)bytes);
@@ -437,9 +452,9 @@ int dalloc(gls_ctx *c, void **p, size_t bytes) {
 }
 
 template <class T>
-int dalloc_n(gls_ctx *c, T **p, size_t n) {
+int dalloc_n(gls_ctx *c, T **p, size_t n, bool persistent = false) {
     void *q = nullptr;
-    int rc = dalloc(c, &q, n * sizeof(T));
+    int rc = dalloc(c, &q, n * sizeof(T), persistent);
     *p = static_cast<T *>(q);
     return rc;
 }
@@ -948,9 +963,9 @@ static int load_general(gls_ctx *c, int32_t n_pi, int32_t n_gates, const int32_t
         n->ext2int.resize(N);
         for (int32_t i = 0; i < n_pi; i++) n->ext2int[i] = i;
         for (int32_t g = 0; g < n_gates; g++) n->ext2int[n_pi + g] = n_pi + n->lv.pos[g];
-        rc = dalloc_n(c, &n->d_gates, recs.size());
-        if (!rc) rc = dalloc_n(c, &n->d_ext2int, (size_t)std::max<int64_t>(N, 1));
-        if (!rc) rc = dalloc_n(c, &n->d_level_begin, n->lv.level_begin.size());
+        rc = dalloc_n(c, &n->d_gates, recs.size(), true);
+        if (!rc) rc = dalloc_n(c, &n->d_ext2int, (size_t)std::max<int64_t>(N, 1), true);
+        if (!rc) rc = dalloc_n(c, &n->d_level_begin, n->lv.level_begin.size(), true);
         if (rc) { free_netlist(c, n.get()); return rc; }
         CK(cudaMemcpyAsync(n->d_level_begin, n->lv.level_begin.data(), sizeof(int32_t) * n->lv.level_begin.size(),
                            cudaMemcpyHostToDevice, c->stream));
@@ -1090,10 +1105,10 @@ int gls_load_stimulus(gls_ctx *c, int32_t n_pi, const int64_t *off, const int32_
         auto s = std::make_unique<StimObj>();
         s->n_pi = n_pi;
         s->cap_events = off[n_pi];
-        rc = dalloc_n(c, &s->d_off, (size_t)n_pi + 1);
-        if (!rc) rc = dalloc_n(c, &s->d_t, (size_t)std::max<int64_t>(s->cap_events, 1));
-        if (!rc) rc = dalloc_n(c, &s->d_v, (size_t)std::max<int64_t>(s->cap_events, 1));
-        if (!rc) rc = dalloc_n(c, &s->d_packed, (size_t)stim_words(s->cap_events, n_pi));
+        rc = dalloc_n(c, &s->d_off, (size_t)n_pi + 1, true);
+        if (!rc) rc = dalloc_n(c, &s->d_t, (size_t)std::max<int64_t>(s->cap_events, 1), true);
+        if (!rc) rc = dalloc_n(c, &s->d_v, (size_t)std::max<int64_t>(s->cap_events, 1), true);
+        if (!rc) rc = dalloc_n(c, &s->d_packed, (size_t)stim_words(s->cap_events, n_pi), true);
         if (!rc) rc = upload_stimulus(c, s.get(), off, t, v);
         if (rc) { free_stim(c, s.get()); return rc; }
         const int32_t id = c->next_id++;
@@ -1364,7 +1379,7 @@ int gls_plan_order(gls_ctx *c, int32_t netlist_id, int32_t run_id, int32_t item)
     std::vector<GateRec> recs((size_t)std::max(G, 1));
     for (int32_t q = 0; q < G; q++) recs[q] = n->recs[order[q]];
     GateRec *d = nullptr;
-    rc = dalloc_n(c, &d, recs.size());
+    rc = dalloc_n(c, &d, recs.size(), true);
     if (rc) return rc;
     n->plans.push_back(d);
     CK(cudaMemcpy(d, recs.data(), sizeof(GateRec) * recs.size(), cudaMemcpyHostToDevice));
@@ -1575,9 +1590,9 @@ int gls_load_stimulus64(gls_ctx *c, int32_t n_pi, const int64_t *off, const int6
         s->cap_events = s->n_events = off[n_pi];
         s->max_time64 = mx;
         const size_t E = (size_t)std::max<int64_t>(s->cap_events, 1);
-        rc = dalloc_n(c, &s->d_off, (size_t)n_pi + 1);
-        if (!rc) rc = dalloc_n(c, &s->d_t64, E);
-        if (!rc) rc = dalloc_n(c, &s->d_v, E);
+        rc = dalloc_n(c, &s->d_off, (size_t)n_pi + 1, true);
+        if (!rc) rc = dalloc_n(c, &s->d_t64, E, true);
+        if (!rc) rc = dalloc_n(c, &s->d_v, E, true);
         if (rc) { free_stim(c, s.get()); return rc; }
         cudaError_t e = cudaMemcpy(s->d_off, off, sizeof(int64_t) * ((size_t)n_pi + 1), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && s->n_events > 0)

@@ -15,8 +15,11 @@ resident stimulus.  The dispatcher:
     request's latency (arrival -> results resident on the device) and
     re-admits a launch whose arena was too small with the measured demand.
 Device buffers come from the context's pool, so admitting and retiring never
-synchronises the device.  batching=False, streams=1 gives the plain form:
-one request per launch, one launch at a time, in arrival order.
+synchronises the device.  policy="sjf" admits the waiting request with the
+least estimated work first (shortest job first: small windows do not queue
+behind large ones); "fifo" admits in arrival order.  batching=False,
+streams=1, policy="fifo" gives the plain form: one request per launch, one
+launch at a time, in arrival order.
 """
 from __future__ import annotations
 
@@ -71,13 +74,16 @@ class ServeStats:
 
 class Server:
     def __init__(self, ctx: Context, budget_bytes: int, max_batch: int = 16, streams: int = 4,
-                 batching: bool = True, safety: float = 1.3, keep_results: bool = False):
+                 batching: bool = True, safety: float = 1.3, keep_results: bool = False, policy: str = "sjf"):
         import torch
         self.ctx = ctx
         self.budget = int(budget_bytes)
         self.max_batch = max_batch if batching else 1
         self.safety = safety
         self.keep = keep_results
+        if policy not in ("sjf", "fifo"):
+            raise ValueError(policy)
+        self.policy = policy
         self.streams = [torch.cuda.Stream() for _ in range(max(1, streams))]
         self.res: dict[str, Resident] = {}
 
@@ -88,10 +94,12 @@ class Server:
         self.res[key] = Resident(key, nid, sid, int(netlist.n_pi + netlist.n_gates), int(stimulus.n_events),
                                  int(window))
 
-    def calibrate(self, frac: float = 0.2):
+    def calibrate(self, frac: float = 0.2, plan: bool = True):
         """Event-arena words per stimulus transition of each resident netlist,
         from one run over the first `frac` of its window (the footprint model
-        of admission; transitions are spread evenly over the window)."""
+        of admission; transitions are spread evenly over the window).  With
+        plan, the same run also plans the netlist's critical-path-first gate
+        order for the dependency schedule (gls_plan_order)."""
         for r in self.res.values():
             t_limit = max(1, int(r.window * frac))
             arena = 0
@@ -100,6 +108,8 @@ class Server:
                 rc, demand, _ = self.ctx.run_stats_raw(rid)
                 if rc == 0:
                     demand = self.ctx.run_info(rid)[0]
+                    if plan:
+                        self.ctx.plan_order(r.nid, rid)
                 self.ctx.release(rid)
                 if rc == 0:
                     break
@@ -178,13 +188,16 @@ class Server:
                 with lock:
                     if not pending:
                         break
-                    head = pending[0]
+                    if self.policy == "sjf":
+                        head = min(pending, key=lambda q: self.estimate_words(q.netlist, q.t_limit))
+                    else:
+                        head = pending[0]
                     group = [head]
                     if self.max_batch > 1:
-                        for q in list(pending)[1:]:
+                        for q in list(pending):
                             if len(group) >= self.max_batch:
                                 break
-                            if q.netlist == head.netlist:
+                            if q is not head and q.netlist == head.netlist:
                                 group.append(q)
                 r = self.res[head.netlist]
                 sc = scale.get(head.netlist, 1.0)

@@ -32,13 +32,13 @@ def residents():
     return out
 
 
-@pytest.mark.parametrize("batching,streams", [(True, 3), (False, 1)])
-def test_served_results_equal_alone_and_oracle(batching, streams):
+@pytest.mark.parametrize("batching,streams,policy", [(True, 3, "sjf"), (True, 3, "fifo"), (False, 1, "fifo")])
+def test_served_results_equal_alone_and_oracle(batching, streams, policy):
     res = residents()
     with gls.Context(0) as ctx:
         ctx.set_option(gls.gls.GLS_OPT_POOL_BYTES, 8 << 30)
         srv = Server(ctx, budget_bytes=4 << 30, max_batch=8, streams=streams, batching=batching,
-                     keep_results=True)
+                     keep_results=True, policy=policy)
         for k, (nl, st) in res.items():
             srv.add_resident(k, nl, st, WINDOW)
         srv.calibrate()
