@@ -399,9 +399,10 @@ int gls_set_option(gls_ctx *ctx, int option, int64_t value);
  * device memory:
  *   d_net_ptr[n_nets]    device u64: address of each net's first transition
  *   d_net_len[n_nets]    device u32: transition count of each net
- *   d_arena[arena_words] device u32: gate output transitions, each
- *                        (time << 2) | value; arena_words >= 64, and the last
- *                        64 words are kept free as read padding
+ *   d_arena[arena_words] device u32, 16-byte aligned: gate output
+ *                        transitions, each (time << 2) | value;
+ *                        arena_words >= 64, and the last 64 words are kept
+ *                        free as read padding
  *   d_report[4]          device u32, written at the end of the run:
  *                        [0] status bits (1 = arena too small, 2 = carried
  *                        transitions beyond GLS_MAX_DELAY_SPREAD, 4 = a time

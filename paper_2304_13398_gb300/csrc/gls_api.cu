@@ -1512,6 +1512,7 @@ int gls_simulate_noalloc(gls_ctx *c, int32_t netlist_id, int32_t stim_id, uint64
     if (n->lv.depth > GLS_NOALLOC_MAX_LEVELS)
         return fail(GLS_ERANGE, "netlist depth %d exceeds the %d levels of the no-allocation scratch",
                     n->lv.depth, GLS_NOALLOC_MAX_LEVELS);
+    if (reinterpret_cast<uintptr_t>(d_arena) & 15u) return fail(GLS_EINVAL, "d_arena must be 16-byte aligned");
     if (arena_words < 2 * (int64_t)kSlotAlign)
         return fail(GLS_EINVAL, "arena of %lld words is below the %u-word minimum", (long long)arena_words,
                     2 * kSlotAlign);

@@ -65,6 +65,7 @@ struct __align__(16) WarpSmem {
     // value (0, 1, X) and set of (pin, edge) pairs changed at the timestamp
     // (bit 2p: pin p rose, bit 2p+1: it fell; both for X<->Z)
     uint8_t dtab[3][64];
+    uint64_t mbar[2];         // completion barriers of the two window buffers
     __device__ __forceinline__ uint32_t *B() { return Q + PCAP; }
     __device__ __forceinline__ uint16_t *Binfo() { return reinterpret_cast<uint16_t *>(Q + PCAP + 2 * CH + 4); }
 };
@@ -76,12 +77,34 @@ struct CommitState {
     int np;              // carried transitions in Q[0..np)
 };
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+// Bulk (TMA) copies of pin windows into shared memory, completed on an
+// mbarrier per window buffer: one lane announces the bytes and issues one
+// copy per pin; every lane waits for the barrier's phase.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+constexpr uint64_t kWindowWaitNs = 2000000000ull;   // bound on one window wait (2 s; a copy takes microseconds)
+
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     uint32_t v;
@@ -95,6 +118,31 @@ __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
     return t;
+}
+
+// Once per warp before its first gate: the window barriers (phase parity 0).
+template <int CH>
+__device__ __forceinline__ void init_window_barriers(WarpSmem<CH> &sm, int lane) {
+    if (lane == 0) {
+        mbar_init(&sm.mbar[0]);
+        mbar_init(&sm.mbar[1]);
+        mbar_init_fence();
+    }
+    __syncwarp();
+}
+
+// Wait for window buffer b (parity bit b of par, flipped on completion);
+// false if the copies did not complete within kWindowWaitNs.
+template <int CH>
+__device__ __forceinline__ bool wait_window(WarpSmem<CH> &sm, int b, uint32_t &par) {
+    const uint32_t ph = (par >> b) & 1u;
+    if (!mbar_try_wait(&sm.mbar[b], ph)) {
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(&sm.mbar[b], ph))
+            if (globaltimer() - t0 > kWindowWaitNs) return false;
+    }
+    par ^= 1u << b;
+    return true;
 }
 
 // Number of elements of L among the first d elements of merge(L, R), where an
@@ -155,22 +203,25 @@ __device__ __forceinline__ uint32_t edge_class(uint32_t old, uint32_t nw) {
 template <int K, int CH>
 __device__ __forceinline__ bool issue_windows(WarpSmem<CH> &sm, int b, const GateCtx &g, const uint32_t *cur,
                                               int *lead, int *n, int lane) {
-    bool any = false;
+    uint32_t bytes[3] = {0u, 0u, 0u}, total = 0;
 #pragma unroll
     for (int p = 0; p < K; p++) {
         const int np = (int)min((uint32_t)CH, g.len[p] - cur[p]);
         n[p] = np;
-        const uint32_t a = cur[p] & ~3u;
-        lead[p] = (int)(cur[p] - a);
+        lead[p] = (int)(cur[p] & 3u);
         if (np > 0) {
-            any = true;
-            const int vecs = (lead[p] + np + 3) >> 2;
-            const uint4 *src = reinterpret_cast<const uint4 *>(g.src[p] + a);
-            for (int v = lane; v < vecs; v += 32) cp_async16(&sm.win[b][p][4 * v], src + v);
+            bytes[p] = (uint32_t)((lead[p] + np + 3) >> 2) * 16u;
+            total += bytes[p];
         }
     }
-    cp_async_commit();
-    return any;
+    if (lane == 0 && total > 0) {
+        fence_proxy_async();   // the warp's earlier reads and writes of buffer b precede the copies
+        mbar_arrive_expect_tx(&sm.mbar[b], total);
+#pragma unroll
+        for (int p = 0; p < K; p++)
+            if (bytes[p]) bulk_load(&sm.win[b][p][0], g.src[p] + (cur[p] & ~3u), bytes[p], &sm.mbar[b]);
+    }
+    return total > 0;
 }
 
 // Steps 4 and 5 of a chunk, shared by every pin count.  Lane l's stack is
@@ -242,8 +293,10 @@ __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0,
     return true;
 }
 
+// Returns false only when a window copy did not complete within its poll
+// bound (the warp then stops: its buffers may still be written).
 template <int K, bool DEP, int CH, bool EDGE>
-__device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane) {
+__device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane, uint32_t &par) {
     GateCtx g;
     uint64_t bound = 0;
 #pragma unroll
@@ -343,7 +396,7 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
             r.net_len[out_net] = 0;
             if (r.st_in) r.st_out[out_net] = r.st_in[out_net];
         }
-        return;
+        return true;
     }
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(r.arena_top, (unsigned long long)((bound + kSlotAlign - 1) & ~(uint64_t)(kSlotAlign - 1)));
@@ -354,7 +407,7 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
             r.net_ptr[out_net] = 0;
             r.net_len[out_net] = 0;
         }
-        return;
+        return true;
     }
     uint32_t *out = r.arena + base;
     if (cs.np > 0) {   // carried transitions, moved to this slice's local time
@@ -376,8 +429,10 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
     const bool any_input = more;
 
     while (more) {
-        cp_async_wait_all();
-        __syncwarp();
+        if (!wait_window(sm, b, par)) {   // the copies never completed: stop this warp
+            if (lane == 0) atomicOr(r.status, kStTimeout);
+            return false;
+        }
         const uint32_t *A[3];
 #pragma unroll
         for (int p = 0; p < 3; p++) A[p] = &sm.win[b][p < K ? p : 0][p < K ? lead[p] : 0];
@@ -577,7 +632,11 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         b ^= 1;
         __syncwarp();
     }
-    if (failed) cp_async_wait_all();   // leave no copy in flight into this warp's buffers
+    // leave no copy in flight into this warp's buffers
+    if (failed && more && !wait_window(sm, b ^ 1, par)) {
+        if (lane == 0) atomicOr(r.status, kStTimeout);
+        return false;
+    }
     if (r.st_in && !failed) {
         // no input transition in this slice: settle the carried ones alone
         if (!any_input) failed = !commit_chunk<CH>(sm, lane, 0, 0, send, out, cs);
@@ -594,22 +653,23 @@ __device__ void eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         r.net_ptr[out_net] = reinterpret_cast<uint64_t>(out);
         r.net_len[out_net] = failed ? 0u : cs.outCount;
     }
+    return true;
 }
 
 template <bool DEP, int CH>
-__device__ __forceinline__ void eval_windowed(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane) {
+__device__ __forceinline__ bool eval_windowed(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane,
+                                              uint32_t &par) {
     if (gr.flags & kGateEdge) {
         switch (gr.k) {
-        case 1: eval_gate<1, DEP, CH, true>(gr, r, sm, lane); break;
-        case 2: eval_gate<2, DEP, CH, true>(gr, r, sm, lane); break;
-        default: eval_gate<3, DEP, CH, true>(gr, r, sm, lane); break;
+        case 1: return eval_gate<1, DEP, CH, true>(gr, r, sm, lane, par);
+        case 2: return eval_gate<2, DEP, CH, true>(gr, r, sm, lane, par);
+        default: return eval_gate<3, DEP, CH, true>(gr, r, sm, lane, par);
         }
-        return;
     }
     switch (gr.k) {
-    case 1: eval_gate<1, DEP, CH, false>(gr, r, sm, lane); break;
-    case 2: eval_gate<2, DEP, CH, false>(gr, r, sm, lane); break;
-    default: eval_gate<3, DEP, CH, false>(gr, r, sm, lane); break;
+    case 1: return eval_gate<1, DEP, CH, false>(gr, r, sm, lane, par);
+    case 2: return eval_gate<2, DEP, CH, false>(gr, r, sm, lane, par);
+    default: return eval_gate<3, DEP, CH, false>(gr, r, sm, lane, par);
     }
 }
 
@@ -905,11 +965,21 @@ __device__ __forceinline__ void eval_segmented(const GateRec &gr, const RunDev &
 
 // V = kVariantSegmented or kVariantWindowed
 template <int V, bool DEP>
-__device__ __forceinline__ void eval_variant(const GateRec &gr, const RunDev &r, unsigned char *smem_raw,
-                                             int warp, int lane) {
-    if (V == kVariantSegmented) seg::eval_segmented<DEP>(gr, r, lane);
-    else if (V == kVariantWindowedWide) eval_windowed<DEP, 256>(gr, r, reinterpret_cast<WarpSmem<256> *>(smem_raw)[warp], lane);
-    else eval_windowed<DEP, 128>(gr, r, reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane);
+__device__ __forceinline__ bool eval_variant(const GateRec &gr, const RunDev &r, unsigned char *smem_raw,
+                                             int warp, int lane, uint32_t &par) {
+    if (V == kVariantSegmented) {
+        seg::eval_segmented<DEP>(gr, r, lane);
+        return true;
+    }
+    if (V == kVariantWindowedWide)
+        return eval_windowed<DEP, 256>(gr, r, reinterpret_cast<WarpSmem<256> *>(smem_raw)[warp], lane, par);
+    return eval_windowed<DEP, 128>(gr, r, reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane, par);
+}
+
+template <int V>
+__device__ __forceinline__ void init_variant(unsigned char *smem_raw, int warp, int lane) {
+    if (V == kVariantWindowedWide) init_window_barriers(reinterpret_cast<WarpSmem<256> *>(smem_raw)[warp], lane);
+    else if (V == kVariantWindowed) init_window_barriers(reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane);
 }
 
 // Gate record of work index g.  With rep > 1 replicas of one netlist the work
@@ -946,13 +1016,15 @@ __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t L = level + 1;
+    init_variant<V>(smem_raw, warp, lane);
+    uint32_t par = 0;   // phase parities of the warp's window barriers
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(r.level_ctr + level, 1);
         g = __shfl_sync(FULL, g, 0);
         if (g >= g_count) break;
         const GateRec gr = fetch_gate(gates, r, (int64_t)g_begin + g, L);
-        eval_variant<V, false>(gr, r, smem_raw, warp, lane);
+        if (!eval_variant<V, false>(gr, r, smem_raw, warp, lane, par)) break;
         __syncwarp();
     }
 }
@@ -970,6 +1042,8 @@ __global__ void __maxnreg__(V == kVariantWindowed ? 72 : 128) dependency_kernel(
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t L = 1;
+    init_variant<V>(smem_raw, warp, lane);
+    uint32_t par = 0;   // phase parities of the warp's window barriers
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(r.level_ctr + ctr_slot, 1);
@@ -989,7 +1063,9 @@ __global__ void __maxnreg__(V == kVariantWindowed ? 72 : 128) dependency_kernel(
         }
         ok = __all_sync(FULL, ok);
         if (ok) {
-            eval_variant<V, true>(gr, r, smem_raw, warp, lane);
+            // a window copy that never completed stops the warp (its readers
+            // then give up their bounded waits)
+            if (!eval_variant<V, true>(gr, r, smem_raw, warp, lane, par)) break;
         } else if (lane == 0) {
             atomicOr(r.status, kStTimeout);
             r.net_ptr[gr.out_net] = 0;
