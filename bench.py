@@ -337,15 +337,23 @@ def run_own(a):
         t_h = torch.from_numpy(st.t).pin_memory()
         v_h = torch.from_numpy(st.v).pin_memory()
         total = int(off[-1])
-        roff = torch.empty(N + 1, dtype=torch.int64).pin_memory()
-        rpk = torch.empty(total, dtype=torch.int32).pin_memory()
         h2d = 8 * (nl.n_pi + 1) + 5 * st.n_events
-        d2h = 8 * (N + 1) + 4 * total
+        # results straight into pinned host memory: a second run of the same
+        # workload whose kernels mirror every output store to the host
+        ctx.set_option(gls.gls.GLS_OPT_HOST_MIRROR, 1)
+        demand = ctx.run_info(rid)[0]
+        mrid = ctx.simulate(nid, sid, arena_events=int(demand * 1.02) + (1 << 20), stream=stream)
+        ctx.run_stats(mrid)
+        ctx.set_option(gls.gls.GLS_OPT_HOST_MIRROR, 0)
+        G = nl.n_gates
+        goff = torch.empty(G, dtype=torch.int64).pin_memory()
+        glen = torch.empty(G, dtype=torch.int32).pin_memory()
+        d2h = 4 * (total - int(off[nl.n_pi])) + 12 * G   # the mirrored gate transitions + descriptors
+
         def e2e_step():
             ctx.update_stimulus(sid, off_h, t_h, v_h)
-            ctx.rerun(rid, stream)
-            ctx.run_stats(rid)
-            ctx.read_all(rid, roff, rpk)
+            ctx.rerun(mrid, stream)
+            ctx.read_host(mrid, 0, goff, glen)
         e2e_step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -359,7 +367,10 @@ def run_own(a):
             e_ms = float(t.item())
         e2e = {"value": world * e_out / (e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms,
-               "timing": "host wall clock over the public calls, pinned host buffers"}
+               "timing": "host wall clock over the public calls, pinned host buffers",
+               "result_path": "gls_read_host: the kernels store every output transition into a pinned host "
+                              "mirror as they go; the step ends when all waveforms and their descriptors are "
+                              "in host memory (primary inputs are the caller's stimulus)"}
 
     peak, peak_kind = measured_peak_gbs()
     achieved = alg_bytes / (k_ms / 1000.0) / 1e9

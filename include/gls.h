@@ -350,6 +350,20 @@ int gls_read_all64(gls_ctx *ctx, int32_t run_id, int64_t *off, int64_t *t, uint8
 int gls_read_waveform64(gls_ctx *ctx, int32_t run_id, int32_t net, int64_t *t, uint8_t *v, int64_t cap,
                         int64_t *n_out);
 
+/*
+ * Results of a run created with GLS_OPT_HOST_MIRROR, without a device-to-host
+ * copy of the waveforms: waits for the run (its error, if it failed), then
+ * *arena = the run's pinned host mirror (valid until the run is evaluated
+ * again or released), and for every gate g of item `item` in caller order
+ * (net n_pi + g) its waveform is (*arena)[gate_off[g] .. gate_off[g] +
+ * gate_len[g]), packed (time << 2) | value as in gls_read_all.  Primary
+ * inputs are the caller's stimulus and are not listed.  gate_off and
+ * gate_len hold n_gates entries (host arrays).  GLS_EINVAL for a run without
+ * a mirror.
+ */
+int gls_read_host(gls_ctx *ctx, int32_t run_id, int32_t item, const uint32_t **arena, int64_t *gate_off,
+                  uint32_t *gate_len);
+
 /* Context options (gls_set_option); they apply to runs created afterwards. */
 typedef enum gls_option {
     GLS_OPT_SCHEDULE = 1,       /* GLS_SCHEDULE_LEVELS or GLS_SCHEDULE_DEPENDENCY (default)  */
@@ -361,6 +375,11 @@ typedef enum gls_option {
     GLS_OPT_KERNEL = 5,         /* GLS_KERNEL_WINDOWED_WIDE (default), _WINDOWED or _SEGMENTED  */
     GLS_OPT_SEGMENT = 6,        /* segmented kernel: input transitions per lane segment, >= 1
                                    (default 32); a gate uses min(32, ceil(inputs / this)) lanes */
+    GLS_OPT_HOST_MIRROR = 8,    /* 1: runs created afterwards (not sliced, windowed kernels)
+                                   also store every output transition into a pinned host mirror
+                                   of their event arena as the kernels write it, so the results
+                                   reach host memory while the simulation runs (gls_read_host);
+                                   0 (default): results stay on the device until read */
     GLS_OPT_POOL_BYTES = 7      /* > 0: allocate one device region of this size now and carve
                                    every later netlist, stimulus and run buffer from it (first
                                    fit, no cudaMalloc/cudaFree per run, so creating and freeing

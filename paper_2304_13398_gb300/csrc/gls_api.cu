@@ -332,6 +332,9 @@ struct RunObj {
     uint32_t *d_gather = nullptr;
     int64_t gather_cap = 0;
     int schedule = 0;
+    uint32_t *h_arena = nullptr;        // pinned host mirror of the arena (GLS_OPT_HOST_MIRROR)
+    uint32_t *d_glen = nullptr;         // [gates] scratch of gls_read_host
+    int64_t glen_cap = 0;
     // time-sliced runs (task division over time)
     int64_t slice_ps = 0;               // 0: not sliced
     uint32_t *d_slice_packed = nullptr; // one slice's primary-input transitions
@@ -359,6 +362,7 @@ struct gls_ctx {
     uint64_t wait_limit_ns = 10ull * 1000 * 1000 * 1000;
     int32_t withhold_gate = -1;
     uint32_t seg_target = 32;
+    bool host_mirror = false;           // GLS_OPT_HOST_MIRROR
     int32_t next_id = 1;
     std::unordered_map<int32_t, std::unique_ptr<NetlistObj>> netlists;
     std::unordered_map<int32_t, std::unique_ptr<StimObj>> stims;
@@ -501,6 +505,8 @@ void free_run(gls_ctx *c, RunObj *r) {
     dfree(c, r->d_scan_tmp);
     dfree(c, r->d_gather);
     dfree(c, r->d_slice_packed);
+    dfree(c, r->d_glen);
+    if (r->h_arena) cudaFreeHost(r->h_arena);
     for (int k = 0; k < 2; k++) {
         dfree(c, r->d_st[k]);
         dfree(c, r->d_pend[k]);
@@ -736,6 +742,23 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
     if (!rc) rc = dalloc_n(c, &r->d_pi_total, 1);
     if (rc) { free_run(c, r.get()); return rc; }
     r->dev.pi_total = r->d_pi_total;
+    if (c->host_mirror && slice_ps == 0) {
+        if (c->cfg.variant == kVariantSegmented) {
+            free_run(c, r.get());
+            return fail(GLS_EINVAL, "host-mirrored results need the windowed kernels");
+        }
+        void *h = nullptr, *d = nullptr;
+        cudaError_t e = cudaHostAlloc(&h, sizeof(uint32_t) * ((size_t)arena_events + 2 * kSlotAlign), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&d, h, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (h) cudaFreeHost(h);
+            free_run(c, r.get());
+            return fail(GLS_ENOMEM, "pinned host mirror of %lld words: %s", (long long)arena_events, cudaGetErrorString(e));
+        }
+        r->h_arena = static_cast<uint32_t *>(h);
+        r->dev.harena = static_cast<uint32_t *>(d);
+    }
     if (slice_ps > 0) {
         const StimObj *s = find_stim(c, stim_ids[0]);
         rc = dalloc_n(c, &r->d_slice_packed, (size_t)stim_words(s->cap_events, s->n_pi));
@@ -1332,6 +1355,50 @@ int run_sliced(gls_ctx *c, RunObj *r, cudaStream_t cs) {
     return GLS_OK;
 }
 
+int gls_read_host(gls_ctx *c, int32_t run_id, int32_t item, const uint32_t **arena, int64_t *gate_off,
+                  uint32_t *gate_len) {
+    if (!c || !arena || !gate_off || !gate_len) return fail(GLS_EINVAL, "NULL argument");
+    RunObj *r = find_run(c, run_id);
+    if (!r) return fail(GLS_EINVAL, "unknown run id %d", run_id);
+    if (!r->h_arena) return fail(GLS_EINVAL, "run %d has no host mirror (set GLS_OPT_HOST_MIRROR before creating it)", run_id);
+    if (item < 0 || item >= (int32_t)r->items.size()) return fail(GLS_EINVAL, "item %d out of range", item);
+    CK(cudaSetDevice(c->device));
+    int rc = run_stats_impl(c, r, nullptr, nullptr);   // waits; a failed run has no complete result
+    if (rc) return rc;
+    const RunItem &it = r->items[item];
+    NetlistObj *n = find_netlist(c, it.netlist_id);
+    const int64_t G = n->n_gates, N = (int64_t)n->n_pi + G;
+    if (r->off_cap < N + 1) {
+        dfree(c, r->d_off);
+        dfree(c, r->d_scan_tmp);
+        r->d_off = nullptr;
+        r->d_scan_tmp = nullptr;
+        r->off_cap = 0;
+        r->scan_tmp = scan_tmp_elems(N + 1);
+        rc = dalloc_n(c, &r->d_off, (size_t)N + 1);
+        if (!rc) rc = dalloc_n(c, &r->d_scan_tmp, r->scan_tmp);
+        if (rc) return rc;
+        r->off_cap = N + 1;
+    }
+    if (r->glen_cap < G) {
+        dfree(c, r->d_glen);
+        r->d_glen = nullptr;
+        r->glen_cap = 0;
+        rc = dalloc_n(c, &r->d_glen, (size_t)std::max<int64_t>(G, 1));
+        if (rc) return rc;
+        r->glen_cap = G;
+    }
+    CK(launch_gather_descriptors(r->dev.net_ptr, r->dev.net_len, n->d_ext2int, n->n_pi, G, it.net_base, r->dev.arena,
+                                 r->d_off, r->d_glen, c->stream));
+    if (G > 0) {
+        CK(cudaMemcpyAsync(gate_off, r->d_off, sizeof(int64_t) * (size_t)G, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(gate_len, r->d_glen, sizeof(uint32_t) * (size_t)G, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    *arena = r->h_arena;
+    return GLS_OK;
+}
+
 // Critical-path-first order for the dependency schedule: w(g) = 64 + the
 // transitions on g's fanin pins in the calibration run, b(g) = w(g) + max b
 // over g's readers (longest weighted path to an output), gates by decreasing
@@ -1461,6 +1528,10 @@ int gls_set_option(gls_ctx *c, int option, int64_t value) {
     case GLS_OPT_SEGMENT:
         if (value < 1 || value > (1 << 20)) return fail(GLS_EINVAL, "segment target must be in [1, 2^20]");
         c->seg_target = (uint32_t)value;
+        return GLS_OK;
+    case GLS_OPT_HOST_MIRROR:
+        if (value != 0 && value != 1) return fail(GLS_EINVAL, "host mirror must be 0 or 1");
+        c->host_mirror = value == 1;
         return GLS_OK;
     case GLS_OPT_POOL_BYTES: {
         if (value < 0) return fail(GLS_EINVAL, "pool size must be >= 0");

@@ -227,9 +227,9 @@ __device__ __forceinline__ bool issue_windows(WarpSmem<CH> &sm, int b, const Gat
 // Steps 4 and 5 of a chunk, shared by every pin count.  Lane l's stack is
 // cand[d0, top).  Returns false when more than PCAP transitions would be
 // carried.
-template <int CH>
+template <int CH, bool MIRROR>
 __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0, int top, uint32_t Tfin, uint32_t *out,
-                                          CommitState &cs) {
+                                          uint32_t *hout, CommitState &cs) {
     const uint32_t lanemask_lt = (1u << lane) - 1u;
     // Eq. 1 across lanes (suffix minimum of the later lanes' smallest t_r)
     // and against the carried transitions (minimum over the whole chunk)
@@ -274,7 +274,11 @@ __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0,
         const uint32_t pv = idx == 0 ? cs.lastV : (idx < nQ ? (sm.Q[idx - 1] & 3u) : 0u);
         const bool keep = fin && ((e & 3u) != pv);
         const uint32_t bk = __ballot_sync(FULL, keep);
-        if (keep) out[outCount + __popc(bk & lanemask_lt)] = e;
+        if (keep) {
+            const uint32_t at = outCount + __popc(bk & lanemask_lt);
+            out[at] = e;
+            if (MIRROR) hout[at] = e;   // the host mirror of the store
+        }
         outCount += __popc(bk);
         nf += __popc(__ballot_sync(FULL, fin));
     }
@@ -295,7 +299,7 @@ __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0,
 
 // Returns false only when a window copy did not complete within its poll
 // bound (the warp then stops: its buffers may still be written).
-template <int K, bool DEP, int CH, bool EDGE>
+template <int K, bool DEP, int CH, bool EDGE, bool MIRROR>
 __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane, uint32_t &par) {
     GateCtx g;
     uint64_t bound = 0;
@@ -410,6 +414,7 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         return true;
     }
     uint32_t *out = r.arena + base;
+    uint32_t *hout = MIRROR ? r.harena + base : nullptr;
     if (cs.np > 0) {   // carried transitions, moved to this slice's local time
         const uint32_t *pp = r.pend_in + (size_t)out_net * PCAP;
         for (int x = lane; x < cs.np; x += 32) sm.Q[x] = pp[x] - (r.slice_shift << 2);
@@ -622,7 +627,7 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
 
         // ---- 4./5. Eq. 1 across lanes, commit, carry ----
         const uint32_t Tfin = min(last ? kTimeInf : Tend + 1u + g.dmin, send);
-        if (!commit_chunk<CH>(sm, lane, d0, top, Tfin, out, cs)) { failed = true; break; }
+        if (!commit_chunk<CH, MIRROR>(sm, lane, d0, top, Tfin, out, hout, cs)) { failed = true; break; }
 #pragma unroll
         for (int p = 0; p < K; p++)
             if (m[p] > 0) carry = setpin(carry, p, A[p][m[p] - 1] & 3u);
@@ -639,7 +644,7 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
     }
     if (r.st_in && !failed) {
         // no input transition in this slice: settle the carried ones alone
-        if (!any_input) failed = !commit_chunk<CH>(sm, lane, 0, 0, send, out, cs);
+        if (!any_input) failed = !commit_chunk<CH, MIRROR>(sm, lane, 0, 0, send, out, hout, cs);
         if (!failed) {
             if (lane == 0)
                 r.st_out[out_net] = (carry ^ 0x2Au) | ((uint32_t)(started || any_input) << 7) | ((cs.lastV ^ kVX) << 8) |
@@ -656,20 +661,20 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
     return true;
 }
 
-template <bool DEP, int CH>
+template <bool DEP, int CH, bool MIRROR>
 __device__ __forceinline__ bool eval_windowed(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane,
                                               uint32_t &par) {
     if (gr.flags & kGateEdge) {
         switch (gr.k) {
-        case 1: return eval_gate<1, DEP, CH, true>(gr, r, sm, lane, par);
-        case 2: return eval_gate<2, DEP, CH, true>(gr, r, sm, lane, par);
-        default: return eval_gate<3, DEP, CH, true>(gr, r, sm, lane, par);
+        case 1: return eval_gate<1, DEP, CH, true, MIRROR>(gr, r, sm, lane, par);
+        case 2: return eval_gate<2, DEP, CH, true, MIRROR>(gr, r, sm, lane, par);
+        default: return eval_gate<3, DEP, CH, true, MIRROR>(gr, r, sm, lane, par);
         }
     }
     switch (gr.k) {
-    case 1: return eval_gate<1, DEP, CH, false>(gr, r, sm, lane, par);
-    case 2: return eval_gate<2, DEP, CH, false>(gr, r, sm, lane, par);
-    default: return eval_gate<3, DEP, CH, false>(gr, r, sm, lane, par);
+    case 1: return eval_gate<1, DEP, CH, false, MIRROR>(gr, r, sm, lane, par);
+    case 2: return eval_gate<2, DEP, CH, false, MIRROR>(gr, r, sm, lane, par);
+    default: return eval_gate<3, DEP, CH, false, MIRROR>(gr, r, sm, lane, par);
     }
 }
 
@@ -964,7 +969,7 @@ __device__ __forceinline__ void eval_segmented(const GateRec &gr, const RunDev &
 }  // namespace seg
 
 // V = kVariantSegmented or kVariantWindowed
-template <int V, bool DEP>
+template <int V, bool DEP, bool MIRROR>
 __device__ __forceinline__ bool eval_variant(const GateRec &gr, const RunDev &r, unsigned char *smem_raw,
                                              int warp, int lane, uint32_t &par) {
     if (V == kVariantSegmented) {
@@ -972,8 +977,8 @@ __device__ __forceinline__ bool eval_variant(const GateRec &gr, const RunDev &r,
         return true;
     }
     if (V == kVariantWindowedWide)
-        return eval_windowed<DEP, 256>(gr, r, reinterpret_cast<WarpSmem<256> *>(smem_raw)[warp], lane, par);
-    return eval_windowed<DEP, 128>(gr, r, reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane, par);
+        return eval_windowed<DEP, 256, MIRROR>(gr, r, reinterpret_cast<WarpSmem<256> *>(smem_raw)[warp], lane, par);
+    return eval_windowed<DEP, 128, MIRROR>(gr, r, reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane, par);
 }
 
 template <int V>
@@ -1010,7 +1015,7 @@ __device__ __forceinline__ GateRec fetch_gate(const GateRec *__restrict__ gates,
     return gr;
 }
 
-template <int V>
+template <int V, bool MIRROR>
 __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin, int32_t g_count,
                              int32_t level, RunDev r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1024,7 +1029,7 @@ __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin,
         g = __shfl_sync(FULL, g, 0);
         if (g >= g_count) break;
         const GateRec gr = fetch_gate(gates, r, (int64_t)g_begin + g, L);
-        if (!eval_variant<V, false>(gr, r, smem_raw, warp, lane, par)) break;
+        if (!eval_variant<V, false, MIRROR>(gr, r, smem_raw, warp, lane, par)) break;
         __syncwarp();
     }
 }
@@ -1037,7 +1042,7 @@ __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin,
 // (shared memory admits 7 CTAs of 4 warps).
 // Completion flags are per net: primary inputs start done, a gate's output
 // net is released once its waveform and descriptor are written.
-template <int V>
+template <int V, bool MIRROR>
 __global__ void __maxnreg__(V == kVariantWindowed ? 72 : 128) dependency_kernel(const GateRec *__restrict__ gates, int32_t n_gates, int32_t ctr_slot, RunDev r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1065,7 +1070,7 @@ __global__ void __maxnreg__(V == kVariantWindowed ? 72 : 128) dependency_kernel(
         if (ok) {
             // a window copy that never completed stops the warp (its readers
             // then give up their bounded waits)
-            if (!eval_variant<V, true>(gr, r, smem_raw, warp, lane, par)) break;
+            if (!eval_variant<V, true, MIRROR>(gr, r, smem_raw, warp, lane, par)) break;
         } else if (lane == 0) {
             atomicOr(r.status, kStTimeout);
             r.net_ptr[gr.out_net] = 0;
@@ -1087,15 +1092,19 @@ size_t gate_smem_bytes(int variant, int warps_per_cta) {
 template <int V>
 static int max_ctas(int warps_per_cta) {
     const size_t sm = gate_smem_bytes(V, warps_per_cta);
-    cudaFuncSetAttribute(level_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(dependency_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(level_kernel<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(dependency_kernel<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(level_kernel<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(dependency_kernel<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (sm > 0) {   // the windowed variants are limited by shared memory: prefer the largest carveout
-        cudaFuncSetAttribute(level_kernel<V>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(dependency_kernel<V>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(level_kernel<V, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(dependency_kernel<V, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(level_kernel<V, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(dependency_kernel<V, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, level_kernel<V>, warps_per_cta * 32, sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dependency_kernel<V>, warps_per_cta * 32, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, level_kernel<V, false>, warps_per_cta * 32, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dependency_kernel<V, false>, warps_per_cta * 32, sm);
     return a < b ? a : b;
 }
 
@@ -1111,11 +1120,14 @@ cudaError_t launch_level(const GateRec *d_gates, int32_t g_begin, int32_t g_coun
     const int ctas = min(cfg.ctas, (g_count + cfg.warps_per_cta - 1) / cfg.warps_per_cta);
     const size_t sm = gate_smem_bytes(cfg.variant, cfg.warps_per_cta);
     if (cfg.variant == kVariantSegmented)
-        level_kernel<kVariantSegmented><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
-    else if (cfg.variant == kVariantWindowedWide)
-        level_kernel<kVariantWindowedWide><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
-    else
-        level_kernel<kVariantWindowed><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
+        level_kernel<kVariantSegmented, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
+    else if (cfg.variant == kVariantWindowedWide) {
+        if (r.harena) level_kernel<kVariantWindowedWide, true><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
+        else level_kernel<kVariantWindowedWide, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
+    } else {
+        if (r.harena) level_kernel<kVariantWindowed, true><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
+        else level_kernel<kVariantWindowed, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, g_begin, g_count, level, r);
+    }
     return cudaGetLastError();
 }
 
@@ -1125,11 +1137,14 @@ cudaError_t launch_dependency(const GateRec *d_gates, int32_t n_gates, int32_t c
     const int ctas = min(cfg.ctas, (n_gates + cfg.warps_per_cta - 1) / cfg.warps_per_cta);
     const size_t sm = gate_smem_bytes(cfg.variant, cfg.warps_per_cta);
     if (cfg.variant == kVariantSegmented)
-        dependency_kernel<kVariantSegmented><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
-    else if (cfg.variant == kVariantWindowedWide)
-        dependency_kernel<kVariantWindowedWide><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
-    else
-        dependency_kernel<kVariantWindowed><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+        dependency_kernel<kVariantSegmented, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+    else if (cfg.variant == kVariantWindowedWide) {
+        if (r.harena) dependency_kernel<kVariantWindowedWide, true><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+        else dependency_kernel<kVariantWindowedWide, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+    } else {
+        if (r.harena) dependency_kernel<kVariantWindowed, true><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+        else dependency_kernel<kVariantWindowed, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+    }
     return cudaGetLastError();
 }
 

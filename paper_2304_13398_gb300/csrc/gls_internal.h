@@ -82,6 +82,8 @@ struct RunDev {
     // holds kPendCap pending transitions per net in the previous slice's
     // local time.
     uint32_t *st_in, *st_out, *pend_in, *pend_out;
+    uint32_t *harena;         // device view of a pinned host mirror of arena (every output word is
+                              // stored there too), or null
     uint32_t slice_end;       // local end of the slice: a t_r at or past it stays pending
     uint32_t slice_shift;     // start of this slice minus start of the previous one
     unsigned long long *pi_total;   // primary-input transitions of the run (after time limits)
@@ -153,6 +155,11 @@ cudaError_t launch_gather_lengths(const uint32_t *d_net_len, const int32_t *d_ex
 cudaError_t launch_exclusive_scan_i64(int64_t *d_data, int64_t n, int64_t *d_tmp, size_t tmp_elems,
                                       cudaStream_t s);
 size_t scan_tmp_elems(int64_t n);
+// Word offset of each gate output (nets net_base + ext2int[n_pi + g]) in the
+// arena and its length, in caller gate order.
+cudaError_t launch_gather_descriptors(const uint64_t *d_net_ptr, const uint32_t *d_net_len, const int32_t *d_ext2int,
+                                      int32_t n_pi, int64_t n_gates, int64_t net_base, const uint32_t *arena,
+                                      int64_t *d_off, uint32_t *d_len, cudaStream_t s);
 cudaError_t launch_gather_events(const uint64_t *d_net_ptr, const uint32_t *d_net_len, const int32_t *d_ext2int,
                                  const int64_t *d_off, int64_t n, uint32_t *d_out, cudaStream_t s,
                                  int64_t net_base = 0);

@@ -83,6 +83,18 @@ __global__ void slice_pack_kernel(const int64_t *__restrict__ off, const TT *__r
     if (lane == 0 && tot) atomicAdd(pi_total, tot);
 }
 
+__global__ void gather_descriptors_kernel(const uint64_t *__restrict__ net_ptr, const uint32_t *__restrict__ net_len,
+                                          const int32_t *__restrict__ ext2int, int32_t n_pi, int64_t n_gates,
+                                          int64_t net_base, const uint32_t *arena, int64_t *off, uint32_t *len) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_gates; g += stride) {
+        const int64_t n = net_base + ext2int[n_pi + g];
+        const uint32_t l = net_len[n];
+        len[g] = l;
+        off[g] = l ? (int64_t)((net_ptr[n] - reinterpret_cast<uint64_t>(arena)) >> 2) : 0;
+    }
+}
+
 // PI net descriptors point into the packed stimulus; everything a run
 // accumulates (counters, status, completion flags) is reset.
 __global__ void run_init_kernel(const int64_t *__restrict__ off, const uint32_t *packed, RunDev r, int32_t n_ctr) {
@@ -237,6 +249,15 @@ cudaError_t launch_slice_pack(const int64_t *d_off, const int32_t *d_t32, const 
     else
         slice_pack_kernel<int32_t><<<grid_for(n_pi, 8), 256, 0, s>>>(d_off, d_t32, d_v, n_pi, T0, T1, d_packed, net_ptr,
                                                                      net_len, done, pi_total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_descriptors(const uint64_t *d_net_ptr, const uint32_t *d_net_len, const int32_t *d_ext2int,
+                                      int32_t n_pi, int64_t n_gates, int64_t net_base, const uint32_t *arena,
+                                      int64_t *d_off, uint32_t *d_len, cudaStream_t s) {
+    if (n_gates <= 0) return cudaSuccess;
+    gather_descriptors_kernel<<<grid_for(n_gates, 256), 256, 0, s>>>(d_net_ptr, d_net_len, d_ext2int, n_pi, n_gates,
+                                                                      net_base, arena, d_off, d_len);
     return cudaGetLastError();
 }
 

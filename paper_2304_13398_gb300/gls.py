@@ -46,6 +46,7 @@ SIGNATURES = [
     ("gls_run_query", ctypes.c_int, [P, i32]),
     ("gls_run_info", ctypes.c_int, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     ("gls_plan_order", ctypes.c_int, [P, i32, i32, i32]),
+    ("gls_read_host", ctypes.c_int, [P, i32, i32, ctypes.POINTER(P), P, P]),
     ("gls_cell_table", ctypes.c_int, [i32, P]),
     ("gls_define_cell", ctypes.c_int, [P, i32, i32, P, ctypes.POINTER(i32)]),
     ("gls_load_netlist_cells", ctypes.c_int, [P, i32, i32, P, P, P, P, ctypes.POINTER(i32)]),
@@ -63,7 +64,7 @@ SIGNATURES = [
     ("gls_release", ctypes.c_int, [P, i32]),
 ]
 GLS_OPT_SCHEDULE, GLS_OPT_WARPS_PER_CTA, GLS_OPT_WAIT_LIMIT_MS, GLS_OPT_TEST_WITHHOLD_GATE, GLS_OPT_KERNEL, GLS_OPT_SEGMENT, \
-    GLS_OPT_POOL_BYTES = 1, 2, 3, 4, 5, 6, 7
+    GLS_OPT_POOL_BYTES, GLS_OPT_HOST_MIRROR = 1, 2, 3, 4, 5, 6, 7, 8
 GLS_KERNEL_SEGMENTED, GLS_KERNEL_WINDOWED, GLS_KERNEL_WINDOWED_WIDE = 0, 1, 2
 KERNELS = {"segmented": GLS_KERNEL_SEGMENTED, "windowed": GLS_KERNEL_WINDOWED, "wide": GLS_KERNEL_WINDOWED_WIDE}
 GLS_SCHEDULE_LEVELS, GLS_SCHEDULE_DEPENDENCY = 0, 1
@@ -158,6 +159,8 @@ class Context:
             raise GlsError(rc, self.lib.gls_last_error(None).decode())
         self.h = h
         self.n_nets = {}
+        self.n_pis = {}          # netlist id -> primary inputs
+        self.run_nets = {}       # run id -> netlist id of each item
 
     def _ck(self, rc):
         if rc:
@@ -198,6 +201,7 @@ class Context:
         self._ck(self.lib.gls_load_netlist(self.h, int(nl.n_pi), len(typ), _p(typ), _p(fo), _p(fn),
                                            _p(dr), _p(df), ctypes.byref(nid)))
         self.n_nets[nid.value] = int(nl.n_pi) + len(typ)
+        self.n_pis[nid.value] = int(nl.n_pi)
         return nid.value
 
     def load_stimulus(self, st, n_pi: int | None = None) -> int:
@@ -227,6 +231,7 @@ class Context:
         self._ck(self.lib.gls_load_netlist_cells(self.h, n_pi, len(ct), _p(ct), _p(fo), _p(fn), _p(d),
                                                  ctypes.byref(nid)))
         self.n_nets[nid.value] = n_pi + self._cell_outputs(ct)
+        self.n_pis[nid.value] = int(n_pi)
         return nid.value
 
     def _cell_outputs(self, ct) -> int:
@@ -256,6 +261,7 @@ class Context:
         self._ck(self.lib.gls_simulate_sliced(self.h, netlist_id, stim_id, int(slice_ps), arena_events,
                                               _stream_handle(stream), ctypes.byref(rid)))
         self.n_nets[rid.value] = self.n_nets[netlist_id]
+        self.run_nets[rid.value] = [netlist_id]
         return rid.value
 
     def run_slices(self, run_id: int) -> int:
@@ -297,6 +303,7 @@ class Context:
         self._ck(self.lib.gls_simulate(self.h, netlist_id, stim_id, arena_events, _stream_handle(stream),
                                        ctypes.byref(rid)))
         self.n_nets[rid.value] = self.n_nets[netlist_id]
+        self.run_nets[rid.value] = [netlist_id]
         return rid.value
 
     def simulate_batch(self, netlist_ids, stim_ids, t_limits=None, arena_events: int = 0, stream=None) -> int:
@@ -310,6 +317,7 @@ class Context:
         self._ck(self.lib.gls_simulate_batch(self.h, len(nids), _p(nids), _p(sids), _p(tls), arena_events,
                                              _stream_handle(stream), ctypes.byref(rid)))
         self.n_nets[rid.value] = [self.n_nets[int(n)] for n in nids]
+        self.run_nets[rid.value] = [int(n) for n in nids]
         return rid.value
 
     def read_item(self, run_id: int, item: int, off=None, packed=None):
@@ -344,6 +352,26 @@ class Context:
         d, c = ctypes.c_int64(0), ctypes.c_int64(0)
         self._ck(self.lib.gls_run_info(self.h, run_id, ctypes.byref(d), ctypes.byref(c)))
         return d.value, c.value
+
+    def read_host(self, run_id: int, item: int = 0, gate_off=None, gate_len=None):
+        """Waveforms of a run created with GLS_OPT_HOST_MIRROR, already in host
+        memory: (arena, gate_off, gate_len) with gate g's packed transitions at
+        arena[gate_off[g]:gate_off[g] + gate_len[g]]; arena is a view of the
+        run's pinned mirror (valid until the run is re-run or released)."""
+        nets = self.run_nets.get(run_id, [])
+        G = 0
+        if 0 <= item < len(nets):   # the library rejects a bad item
+            G = self.n_nets[nets[item]] - self.n_pis[nets[item]]
+        if gate_off is None:
+            gate_off = np.zeros(max(G, 1), np.int64)
+        if gate_len is None:
+            gate_len = np.zeros(max(G, 1), np.uint32)
+        ptr = P()
+        self._ck(self.lib.gls_read_host(self.h, run_id, item, ctypes.byref(ptr), _ptr(gate_off, np.int64),
+                                        _ptr(gate_len, np.uint32)))
+        _, cap = self.run_info(run_id)
+        arena = np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctypes.c_uint32)), shape=(cap,))
+        return arena, gate_off[:G], gate_len[:G]
 
     def plan_order(self, netlist_id: int, run_id: int = -1, item: int = 0):
         """Critical-path-first dependency order for netlist_id from the net
