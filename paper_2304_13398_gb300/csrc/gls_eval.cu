@@ -68,6 +68,13 @@ struct __align__(16) WarpSmem {
     uint64_t mbar[2];         // completion barriers of the two window buffers
     __device__ __forceinline__ uint32_t *B() { return Q + PCAP; }
     __device__ __forceinline__ uint16_t *Binfo() { return reinterpret_cast<uint16_t *>(Q + PCAP + 2 * CH + 4); }
+    // A K-pin cell spreads the three windows of a buffer over its K pins:
+    // chunk<K>() transitions per pin (3 CH, 1.5 CH rounded to 32, CH), so
+    // one- and two-input cells take fewer, longer chunks.
+    template <int K>
+    __host__ __device__ static constexpr int chunk() { return K == 3 ? CH : (K == 2 ? (3 * CH / 2) & ~31 : 3 * CH); }
+    template <int K>
+    __device__ __forceinline__ uint32_t *window(int b, int p) { return &win[b][0][0] + p * (chunk<K>() + 8); }
 };
 
 // Running state of one gate's output between chunks.
@@ -206,7 +213,7 @@ __device__ __forceinline__ bool issue_windows(WarpSmem<CH> &sm, int b, const Gat
     uint32_t bytes[3] = {0u, 0u, 0u}, total = 0;
 #pragma unroll
     for (int p = 0; p < K; p++) {
-        const int np = (int)min((uint32_t)CH, g.len[p] - cur[p]);
+        const int np = (int)min((uint32_t)WarpSmem<CH>::template chunk<K>(), g.len[p] - cur[p]);
         n[p] = np;
         lead[p] = (int)(cur[p] & 3u);
         if (np > 0) {
@@ -219,7 +226,7 @@ __device__ __forceinline__ bool issue_windows(WarpSmem<CH> &sm, int b, const Gat
         mbar_arrive_expect_tx(&sm.mbar[b], total);
 #pragma unroll
         for (int p = 0; p < K; p++)
-            if (bytes[p]) bulk_load(&sm.win[b][p][0], g.src[p] + (cur[p] & ~3u), bytes[p], &sm.mbar[b]);
+            if (bytes[p]) bulk_load(sm.template window<K>(b, p), g.src[p] + (cur[p] & ~3u), bytes[p], &sm.mbar[b]);
     }
     return total > 0;
 }
@@ -440,7 +447,7 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         }
         const uint32_t *A[3];
 #pragma unroll
-        for (int p = 0; p < 3; p++) A[p] = &sm.win[b][p < K ? p : 0][p < K ? lead[p] : 0];
+        for (int p = 0; p < 3; p++) A[p] = sm.template window<K>(b, p < K ? p : 0) + (p < K ? lead[p] : 0);
 
         // ---- 1. chunk cut ----
         uint32_t Tend = kTimeInf;
@@ -456,7 +463,7 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
             // m[p] = transitions of window p at or before Tend (a prefix):
             // count the S-blocks whose last transition qualifies, then the
             // qualifying transitions of the first block that does not
-            constexpr int S = CH / 32;
+            constexpr int S = WarpSmem<CH>::template chunk<K>() / 32;
             int q[3];
 #pragma unroll
             for (int p = 0; p < K; p++) {
@@ -484,7 +491,7 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         more = issue_windows<K, CH>(sm, b ^ 1, g, ncur, nlead, nn, lane);
         if (lane < K) {   // sentinels after the consumed part of every window
             const int at = lane == 0 ? lead[0] + m[0] : (lane == 1 ? lead[1] + m[1] : lead[2] + m[2]);
-            sm.win[b][lane][at] = EINF;
+            sm.template window<K>(b, lane)[at] = EINF;
         }
         __syncwarp();
 
