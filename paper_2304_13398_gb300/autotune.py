@@ -1,8 +1,9 @@
 """Autotuner: pick the gate-kernel configuration for a workload by timing.
 
-Candidates vary how a gate's work is split (one warp per gate with 128- or
-256-transition windows, i.e. the event chunk size; or one lane per time
-segment with a given segment size) and the CTA shape.  Each candidate builds
+Candidates vary how a gate's work is split (one warp per gate with windows
+of 128 or 320 transitions per pin of 3-input cells, longer for fewer
+inputs, i.e. the event chunk size; or one lane per time segment with a
+given segment size) and the CTA shape.  Each candidate builds
 the caller's run, runs it once to warm up, then times `reruns` evaluations
 with the library's own device timer; the fastest configuration is left
 applied to the context and returned.  Results are identical for every

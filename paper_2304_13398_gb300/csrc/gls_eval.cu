@@ -2,11 +2,12 @@
 //
 // For a gate with K <= 3 fanin waveforms the warp streams the fanins in
 // chunks through shared memory.  Per chunk:
-//   1. a window of up to CH transitions of every pin sits in shared memory
-//      (copied asynchronously with 16-byte cp.async while the previous chunk
-//      was being evaluated); the chunk is cut at T_end, the earliest window
-//      end among pins with more transitions left, so every transition at
-//      t <= T_end is present and a timestamp never straddles two chunks;
+//   1. a window of up to 3 CH / K transitions of every pin sits in shared
+//      memory (one bulk copy per pin, completed on an mbarrier, issued as
+//      soon as the previous chunk's walk was done with the windows, so it
+//      overlaps that chunk's commit); the chunk is cut at T_end, the earliest
+//      window end among pins with more transitions left, so every transition
+//      at t <= T_end is present and a timestamp never straddles two chunks;
 //   2. the pins are merged by time with merge-path partitions (pins a and b
 //      first for 3-input cells), each lane taking an equal share; an
 //      all-ones sentinel after every window removes bounds checks;
@@ -27,14 +28,14 @@
 //
 // Output allocation: before evaluating, the warp reserves the Eq. 2 bound
 // (sum of fanin lengths >= distinct input timestamps >= output length),
-// rounded up to 4 words, from the run's event arena with one atomicAdd and
+// rounded up to 32 words, from the run's event arena with one atomicAdd and
 // records (address, length) in the net descriptors when done.
 //
 // Two schedules share the gate code:
 //   level mode       one launch per level (captured in one CUDA graph); the
 //                    launch boundary orders a level after the one before;
 //   dependency mode  one persistent launch for all gates (Algorithm 1): a
-//                    warp takes the next gate in level order and waits, with
+//                    warp takes the next gate in a topological order and waits, with
 //                    a bounded spin, until each fanin gate has published its
 //                    waveform (release/acquire flags), so no level barrier
 //                    holds work back behind the longest gate of a level.
@@ -53,7 +54,7 @@ constexpr uint32_t EINF = 0xFFFFFFFFu;  // sentinel event; its time 2^30-1 excee
 template <int CH>
 struct __align__(16) WarpSmem {
     static constexpr int WIN = CH + 8;     // aligned lead (<= 3) + CH + sentinel, multiple of 4
-    uint32_t win[2][3][WIN];  // double-buffered pin windows
+    uint32_t win[1][3][WIN];  // pin windows (refilled while the chunk's survivors are committed)
     uint32_t cand[3 * CH];    // per-lane stacks of scheduled transitions (t_r << 2 | v)
     // Q: carried transitions (front, at most PCAP) + this chunk's survivors
     // (at most 3 CH).  The survivors are written only after the walk, so the
@@ -74,7 +75,7 @@ struct __align__(16) WarpSmem {
     template <int K>
     __host__ __device__ static constexpr int chunk() { return K == 3 ? CH : (K == 2 ? (3 * CH / 2) & ~31 : 3 * CH); }
     template <int K>
-    __device__ __forceinline__ uint32_t *window(int b, int p) { return &win[b][0][0] + p * (chunk<K>() + 8); }
+    __device__ __forceinline__ uint32_t *window(int b, int p) { return &win[0][0][0] + p * (chunk<K>() + 8); }
 };
 
 // Running state of one gate's output between chunks.
@@ -483,12 +484,10 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
                 if (m[p] > 0) tmx = max(tmx, A[p][m[p] - 1] >> 2);
             if (tmx + g.dmax >= kTimeLimit) atomicOr(r.status, kStTimeRange);
         }
-        // start the copies of the next chunk before evaluating this one
         uint32_t ncur[3] = {cur[0], cur[1], cur[2]};
 #pragma unroll
         for (int p = 0; p < K; p++) ncur[p] += (uint32_t)m[p];
         int nlead[3] = {0, 0, 0}, nn[3] = {0, 0, 0};
-        more = issue_windows<K, CH>(sm, b ^ 1, g, ncur, nlead, nn, lane);
         if (lane < K) {   // sentinels after the consumed part of every window
             const int at = lane == 0 ? lead[0] + m[0] : (lane == 1 ? lead[1] + m[1] : lead[2] + m[2]);
             sm.template window<K>(b, lane)[at] = EINF;
@@ -632,20 +631,24 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
             }
         }
 
-        // ---- 4./5. Eq. 1 across lanes, commit, carry ----
-        const uint32_t Tfin = min(last ? kTimeInf : Tend + 1u + g.dmin, send);
-        if (!commit_chunk<CH, MIRROR>(sm, lane, d0, top, Tfin, out, hout, cs)) { failed = true; break; }
+        // the windows are consumed: refill them for the next chunk while this
+        // one's survivors are committed
 #pragma unroll
         for (int p = 0; p < K; p++)
             if (m[p] > 0) carry = setpin(carry, p, A[p][m[p] - 1] & 3u);
+        __syncwarp();
+        more = issue_windows<K, CH>(sm, 0, g, ncur, nlead, nn, lane);
+
+        // ---- 4./5. Eq. 1 across lanes, commit, carry ----
+        const uint32_t Tfin = min(last ? kTimeInf : Tend + 1u + g.dmin, send);
+        if (!commit_chunk<CH, MIRROR>(sm, lane, d0, top, Tfin, out, hout, cs)) { failed = true; break; }
         started = true;
 #pragma unroll
         for (int p = 0; p < 3; p++) { cur[p] = ncur[p]; lead[p] = nlead[p]; n[p] = nn[p]; }
-        b ^= 1;
         __syncwarp();
     }
     // leave no copy in flight into this warp's buffers
-    if (failed && more && !wait_window(sm, b ^ 1, par)) {
+    if (failed && more && !wait_window(sm, b, par)) {
         if (lane == 0) atomicOr(r.status, kStTimeout);
         return false;
     }
@@ -984,13 +987,13 @@ __device__ __forceinline__ bool eval_variant(const GateRec &gr, const RunDev &r,
         return true;
     }
     if (V == kVariantWindowedWide)
-        return eval_windowed<DEP, 256, MIRROR>(gr, r, reinterpret_cast<WarpSmem<256> *>(smem_raw)[warp], lane, par);
+        return eval_windowed<DEP, 320, MIRROR>(gr, r, reinterpret_cast<WarpSmem<320> *>(smem_raw)[warp], lane, par);
     return eval_windowed<DEP, 128, MIRROR>(gr, r, reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane, par);
 }
 
 template <int V>
 __device__ __forceinline__ void init_variant(unsigned char *smem_raw, int warp, int lane) {
-    if (V == kVariantWindowedWide) init_window_barriers(reinterpret_cast<WarpSmem<256> *>(smem_raw)[warp], lane);
+    if (V == kVariantWindowedWide) init_window_barriers(reinterpret_cast<WarpSmem<320> *>(smem_raw)[warp], lane);
     else if (V == kVariantWindowed) init_window_barriers(reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane);
 }
 
@@ -1093,7 +1096,7 @@ __global__ void __maxnreg__(V == kVariantWindowed ? 72 : 128) dependency_kernel(
 
 size_t gate_smem_bytes(int variant, int warps_per_cta) {
     if (variant == kVariantSegmented) return 0;
-    return (variant == kVariantWindowedWide ? sizeof(WarpSmem<256>) : sizeof(WarpSmem<128>)) * (size_t)warps_per_cta;
+    return (variant == kVariantWindowedWide ? sizeof(WarpSmem<320>) : sizeof(WarpSmem<128>)) * (size_t)warps_per_cta;
 }
 
 template <int V>
