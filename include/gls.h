@@ -391,7 +391,7 @@ typedef enum gls_option {
    SEGMENTED: each lane of a warp evaluates one time segment of the gate
    sequentially and the segments are reconciled once per gate.
    WINDOWED / WINDOWED_WIDE: the warp streams shared-memory windows of 128 /
-   320 transitions per pin of 3-input cells (1.5x for 2-input, 3x for
+   352 transitions per pin of 3-input cells (1.5x for 2-input, 3x for
    1-input cells) and merges, evaluates and filters each window
    cooperatively. */
 enum { GLS_KERNEL_SEGMENTED = 0, GLS_KERNEL_WINDOWED = 1, GLS_KERNEL_WINDOWED_WIDE = 2 };

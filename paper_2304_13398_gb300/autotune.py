@@ -1,7 +1,7 @@
 """Autotuner: pick the gate-kernel configuration for a workload by timing.
 
 Candidates vary how a gate's work is split (one warp per gate with windows
-of 128 or 320 transitions per pin of 3-input cells, longer for fewer
+of 128 or 352 transitions per pin of 3-input cells, longer for fewer
 inputs, i.e. the event chunk size; or one lane per time segment with a
 given segment size) and the CTA shape.  Each candidate builds
 the caller's run, runs it once to warm up, then times `reruns` evaluations

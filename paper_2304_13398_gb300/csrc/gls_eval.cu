@@ -987,13 +987,13 @@ __device__ __forceinline__ bool eval_variant(const GateRec &gr, const RunDev &r,
         return true;
     }
     if (V == kVariantWindowedWide)
-        return eval_windowed<DEP, 320, MIRROR>(gr, r, reinterpret_cast<WarpSmem<320> *>(smem_raw)[warp], lane, par);
+        return eval_windowed<DEP, 352, MIRROR>(gr, r, reinterpret_cast<WarpSmem<352> *>(smem_raw)[warp], lane, par);
     return eval_windowed<DEP, 128, MIRROR>(gr, r, reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane, par);
 }
 
 template <int V>
 __device__ __forceinline__ void init_variant(unsigned char *smem_raw, int warp, int lane) {
-    if (V == kVariantWindowedWide) init_window_barriers(reinterpret_cast<WarpSmem<320> *>(smem_raw)[warp], lane);
+    if (V == kVariantWindowedWide) init_window_barriers(reinterpret_cast<WarpSmem<352> *>(smem_raw)[warp], lane);
     else if (V == kVariantWindowed) init_window_barriers(reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane);
 }
 
@@ -1096,7 +1096,7 @@ __global__ void __maxnreg__(V == kVariantWindowed ? 72 : 128) dependency_kernel(
 
 size_t gate_smem_bytes(int variant, int warps_per_cta) {
     if (variant == kVariantSegmented) return 0;
-    return (variant == kVariantWindowedWide ? sizeof(WarpSmem<320>) : sizeof(WarpSmem<128>)) * (size_t)warps_per_cta;
+    return (variant == kVariantWindowedWide ? sizeof(WarpSmem<352>) : sizeof(WarpSmem<128>)) * (size_t)warps_per_cta;
 }
 
 template <int V>
