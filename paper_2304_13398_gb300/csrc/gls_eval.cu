@@ -269,17 +269,21 @@ __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0,
     const int total = (int)__shfl_sync(FULL, pre, 31);
     const int pos = npk + (int)(pre - cnt);
     __syncwarp();
+#pragma unroll 4
     for (uint32_t x = 0; x < cnt; x++) sm.Q[pos + x] = sm.cand[d0 + x];
     const int nQ = npk + total;
     __syncwarp();
     // commit the final prefix (t_r < Tfin), dropping repeats (Fig. 6)
     int nf = 0;
     uint32_t outCount = cs.outCount;
+    uint32_t vlast = cs.lastV;   // value of the element before this round
     for (int b0 = 0; b0 < nQ; b0 += 32) {
         const int idx = b0 + lane;
         const uint32_t e = idx < nQ ? sm.Q[idx] : 0u;
         const bool fin = idx < nQ && (e >> 2) < Tfin;
-        const uint32_t pv = idx == 0 ? cs.lastV : (idx < nQ ? (sm.Q[idx - 1] & 3u) : 0u);
+        const uint32_t up = __shfl_up_sync(FULL, e & 3u, 1);
+        const uint32_t pv = lane == 0 ? vlast : up;
+        vlast = __shfl_sync(FULL, e & 3u, 31);
         const bool keep = fin && ((e & 3u) != pv);
         const uint32_t bk = __ballot_sync(FULL, keep);
         if (keep) {
@@ -288,7 +292,9 @@ __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0,
             if (MIRROR) hout[at] = e;   // the host mirror of the store
         }
         outCount += __popc(bk);
-        nf += __popc(__ballot_sync(FULL, fin));
+        const uint32_t bf = __ballot_sync(FULL, fin);
+        nf += __popc(bf);
+        if (bf != FULL) break;   // the final ones are a prefix: the rest stays pending
     }
     cs.outCount = outCount;
     if (nf > 0) cs.lastV = sm.Q[nf - 1] & 3u;
