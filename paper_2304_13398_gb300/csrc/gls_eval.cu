@@ -222,12 +222,14 @@ __device__ __forceinline__ bool issue_windows(WarpSmem<CH> &sm, int b, const Gat
             total += bytes[p];
         }
     }
-    if (lane == 0 && total > 0) {
+    if (total > 0 && lane < K) {
         fence_proxy_async();   // the warp's earlier reads and writes of buffer b precede the copies
-        mbar_arrive_expect_tx(&sm.mbar[b], total);
-#pragma unroll
-        for (int p = 0; p < K; p++)
-            if (bytes[p]) bulk_load(sm.template window<K>(b, p), g.src[p] + (cur[p] & ~3u), bytes[p], &sm.mbar[b]);
+        if (lane == 0) mbar_arrive_expect_tx(&sm.mbar[b], total);
+        // one lane per pin
+        const uint32_t by = lane == 0 ? bytes[0] : (lane == 1 ? bytes[1] : bytes[2]);
+        const uint32_t cu = lane == 0 ? cur[0] : (lane == 1 ? cur[1] : cur[2]);
+        const uint32_t *src = lane == 0 ? g.src[0] : (lane == 1 ? g.src[1] : g.src[2]);
+        if (by) bulk_load(sm.template window<K>(b, lane), src + (cu & ~3u), by, &sm.mbar[b]);
     }
     return total > 0;
 }
@@ -614,11 +616,12 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
                 hl = tl ? y : hl;
                 hr = tl ? hr : y;
                 if (K == 3) hinfo = sm.Binfo()[i];
-                const uint32_t t = e >> 2;
+                const uint32_t t = e >> 2, v = e & 3u;
                 uint32_t bit;
-                if (EDGE) bit = edge_class((st >> (2 * pin)) & 3u, e & 3u) << (2 * pin);
-                else bit = 1u << pin;
-                st = setpin(st, (int)pin, e & 3u);
+                if (EDGE) bit = edge_class((st >> (2 * pin)) & 3u, v) << (2 * pin);
+                else bit = K == 2 ? (tl ? 1u : 2u) : 1u << pin;
+                if (K == 2) st = tl ? ((st & ~3u) | v) : ((st & ~12u) | (v << 2));
+                else st = setpin(st, (int)pin, v);
                 grp = (gend ? 0u : grp) | bit;
                 const bool end = (min(hl, hr) >> 2) != t;   // last transition at this time
                 const uint32_t F = K == 3 ? (uint32_t)(((st & 32u) ? g.lut_hi : g.lut_lo) >> (2 * (st & 31u))) & 3u
