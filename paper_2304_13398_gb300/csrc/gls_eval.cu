@@ -66,6 +66,9 @@ struct __align__(16) WarpSmem {
     // value (0, 1, X) and set of (pin, edge) pairs changed at the timestamp
     // (bit 2p: pin p rose, bit 2p+1: it fell; both for X<->Z)
     uint8_t dtab[3][64];
+    // two-input cells: (delay - dmin) << 2 | new value, by changed-pin set
+    // (bits 4-5) and pin values (bits 0-3)
+    uint16_t ftab[64];
     uint64_t mbar[2];         // completion barriers of the two window buffers
     __device__ __forceinline__ uint32_t *B() { return Q + PCAP; }
     __device__ __forceinline__ uint16_t *Binfo() { return reinterpret_cast<uint16_t *>(Q + PCAP + 2 * CH + 4); }
@@ -374,6 +377,14 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         }
         g.dx_lo = __vminu4(g.df_lo, g.dr_lo);
         g.dx_hi = __vminu4(g.df_hi, g.dr_hi);
+        if (K == 2) {
+            const uint32_t l2 = (uint32_t)g.lut_hi;
+            for (int x = lane; x < 64; x += 32) {
+                const uint32_t F = (l2 >> (2 * (x & 15))) & 3u, grp = (uint32_t)x >> 4;
+                sm.ftab[x] = (uint16_t)(((group_delay<2>(g, F, grp) - g.dmin) << 2) | F);
+            }
+            __syncwarp();
+        }
     } else {
         for (int x = lane; x < 192; x += 32) {
             const int F = x >> 6, vm = x & 63;
@@ -624,10 +635,17 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
                 else st = setpin(st, (int)pin, v);
                 grp = (gend ? 0u : grp) | bit;
                 const bool end = (min(hl, hr) >> 2) != t;   // last transition at this time
-                const uint32_t F = K == 3 ? (uint32_t)(((st & 32u) ? g.lut_hi : g.lut_lo) >> (2 * (st & 31u))) & 3u
-                                          : (lut2 >> (2 * (st & 15u))) & 3u;
+                uint32_t F, key;
+                if (K == 2 && !EDGE) {
+                    const uint32_t te = sm.ftab[(grp << 4) | (st & 15u)];
+                    F = te & 3u;
+                    key = (t + g.dmin + (te >> 2)) << 2;
+                } else {
+                    F = K == 3 ? (uint32_t)(((st & 32u) ? g.lut_hi : g.lut_lo) >> (2 * (st & 31u))) & 3u
+                               : (lut2 >> (2 * (st & 15u))) & 3u;
+                    key = (t + (EDGE ? g.dmin + sm.dtab[F][grp] : group_delay<K>(g, F, grp))) << 2;
+                }
                 const bool chg = end && F != Fprev;
-                const uint32_t key = (t + (EDGE ? g.dmin + sm.dtab[F][grp] : group_delay<K>(g, F, grp))) << 2;
                 while (chg && top > d0 && topv >= key) {
                     top--;
                     topv = top > d0 ? sm.cand[top - 1] : 0u;
