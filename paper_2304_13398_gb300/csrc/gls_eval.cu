@@ -377,6 +377,13 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         }
         g.dx_lo = __vminu4(g.df_lo, g.dr_lo);
         g.dx_hi = __vminu4(g.df_hi, g.dr_hi);
+        if (K == 3) {   // delay - dmin by new value and changed-pin set
+            for (int x = lane; x < 24; x += 32) {
+                const uint32_t F = (uint32_t)x >> 3, grp = (uint32_t)x & 7u;
+                sm.dtab[F][grp] = (uint8_t)(group_delay<3>(g, F, grp) - g.dmin);
+            }
+            __syncwarp();
+        }
         if (K == 2) {
             const uint32_t l2 = (uint32_t)g.lut_hi;
             for (int x = lane; x < 64; x += 32) {
@@ -643,7 +650,7 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
                 } else {
                     F = K == 3 ? (uint32_t)(((st & 32u) ? g.lut_hi : g.lut_lo) >> (2 * (st & 31u))) & 3u
                                : (lut2 >> (2 * (st & 15u))) & 3u;
-                    key = (t + (EDGE ? g.dmin + sm.dtab[F][grp] : group_delay<K>(g, F, grp))) << 2;
+                    key = (t + (EDGE || K == 3 ? g.dmin + sm.dtab[F][grp] : group_delay<K>(g, F, grp))) << 2;
                 }
                 const bool chg = end && F != Fprev;
                 while (chg && top > d0 && topv >= key) {
