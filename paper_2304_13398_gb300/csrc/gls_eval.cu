@@ -69,6 +69,7 @@ struct __align__(16) WarpSmem {
     // two-input cells: (delay - dmin) << 2 | new value, by changed-pin set
     // (bits 4-5) and pin values (bits 0-3)
     uint16_t ftab[64];
+    uint8_t f3[64];           // three-input cells: the value for each of the 64 pin-value states
     uint64_t mbar[2];         // completion barriers of the two window buffers
     __device__ __forceinline__ uint32_t *B() { return Q + PCAP; }
     __device__ __forceinline__ uint16_t *Binfo() { return reinterpret_cast<uint16_t *>(Q + PCAP + 2 * CH + 4); }
@@ -377,11 +378,13 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         }
         g.dx_lo = __vminu4(g.df_lo, g.dr_lo);
         g.dx_hi = __vminu4(g.df_hi, g.dr_hi);
-        if (K == 3) {   // delay - dmin by new value and changed-pin set
+        if (K == 3) {   // delay - dmin by new value and changed-pin set; value by pin values
             for (int x = lane; x < 24; x += 32) {
                 const uint32_t F = (uint32_t)x >> 3, grp = (uint32_t)x & 7u;
                 sm.dtab[F][grp] = (uint8_t)(group_delay<3>(g, F, grp) - g.dmin);
             }
+            for (int x = lane; x < 64; x += 32)
+                sm.f3[x] = (uint8_t)((((x & 32) ? g.lut_hi : g.lut_lo) >> (2 * (x & 31))) & 3u);
             __syncwarp();
         }
         if (K == 2) {
@@ -648,7 +651,8 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
                     F = te & 3u;
                     key = (t + g.dmin + (te >> 2)) << 2;
                 } else {
-                    F = K == 3 ? (uint32_t)(((st & 32u) ? g.lut_hi : g.lut_lo) >> (2 * (st & 31u))) & 3u
+                    F = K == 3 ? (EDGE ? (uint32_t)(((st & 32u) ? g.lut_hi : g.lut_lo) >> (2 * (st & 31u))) & 3u
+                                       : (uint32_t)sm.f3[st & 63u])
                                : (lut2 >> (2 * (st & 15u))) & 3u;
                     key = (t + (EDGE || K == 3 ? g.dmin + sm.dtab[F][grp] : group_delay<K>(g, F, grp))) << 2;
                 }
