@@ -96,6 +96,18 @@ def dist_env():
     return rank, world, local
 
 
+def replica_reduce(x: float, op: str, device: str) -> float:
+    """MAX or SUM of x over the replica ranks (x itself on a single rank):
+    the slowest rank's time, the transitions of all ranks."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def describe(name, w):
     r = w.recipe
     nl, st = w.netlist, w.stimulus
@@ -324,11 +336,9 @@ def run_own(a):
         ctx.rerun(rid, stream)
         kernel_ms.append(ctx.run_stats(rid).kernel_ms)
     k_ms = statistics.median(kernel_ms)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * e_out / (ms / 1000.0)
+    ms = replica_reduce(ms, "max", "cuda")
+    all_out = replica_reduce(e_out, "sum", "cuda")   # every replica's transitions
+    value = all_out / (ms / 1000.0)
 
     e2e = None
     if not a.no_e2e:
@@ -361,11 +371,8 @@ def run_own(a):
             e2e_step()
         torch.cuda.synchronize()
         e_ms = (time.perf_counter() - t0) * 1000 / a.e2e_steps
-        if world > 1:
-            t = torch.tensor([e_ms], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * e_out / (e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e_ms = replica_reduce(e_ms, "max", "cuda")
+        e2e = {"value": all_out / (e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms,
                "timing": "host wall clock over the public calls, pinned host buffers",
                "result_path": "gls_read_host: the kernels store every output transition into a pinned host "
