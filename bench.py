@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--long-window", type=int, default=2_970_000_000,
                     help="sliced mode: duration of the long (64-bit time) stimulus, ps")
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--cpu-frac", type=float, default=0.005,
+    ap.add_argument("--cpu-frac", type=float, default=0.012,
                     help="time-window fraction of the CPU-oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
