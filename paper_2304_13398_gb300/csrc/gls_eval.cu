@@ -70,7 +70,7 @@ struct __align__(16) WarpSmem {
     // (bits 4-5) and pin values (bits 0-3)
     uint16_t ftab[64];
     uint8_t f3[64];           // three-input cells: the value for each of the 64 pin-value states
-    uint64_t mbar[2];         // completion barriers of the two window buffers
+    uint64_t mbar[1];         // completion barrier of the window buffer
     __device__ __forceinline__ uint32_t *B() { return Q + PCAP; }
     __device__ __forceinline__ uint16_t *Binfo() { return reinterpret_cast<uint16_t *>(Q + PCAP + 2 * CH + 4); }
     // A K-pin cell spreads the three windows of a buffer over its K pins:
@@ -89,9 +89,9 @@ struct CommitState {
     int np;              // carried transitions in Q[0..np)
 };
 
-// Bulk (TMA) copies of pin windows into shared memory, completed on an
-// mbarrier per window buffer: one lane announces the bytes and issues one
-// copy per pin; every lane waits for the barrier's phase.
+// Bulk (TMA) copies of pin windows into shared memory, completed on the
+// window buffer's mbarrier: lane 0 announces the bytes, lane p issues pin
+// p's copy, every lane waits for the barrier's phase.
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t *bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
@@ -132,12 +132,11 @@ __device__ __forceinline__ uint64_t globaltimer() {
     return t;
 }
 
-// Once per warp before its first gate: the window barriers (phase parity 0).
+// Once per warp before its first gate: the window barrier (phase parity 0).
 template <int CH>
 __device__ __forceinline__ void init_window_barriers(WarpSmem<CH> &sm, int lane) {
     if (lane == 0) {
         mbar_init(&sm.mbar[0]);
-        mbar_init(&sm.mbar[1]);
         mbar_init_fence();
     }
     __syncwarp();
@@ -465,7 +464,7 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
 
     uint32_t cur[3] = {0, 0, 0};
     bool failed = false;
-    int b = 0;
+    const int b = 0;   // the one window buffer
     int lead[3] = {0, 0, 0}, n[3] = {0, 0, 0};
     bool more = issue_windows<K, CH>(sm, 0, g, cur, lead, n, lane);
     const bool any_input = more;
