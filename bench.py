@@ -237,6 +237,25 @@ def cpu_baseline(name, seed, frac):
             "seconds": round(dt, 2), "output_transitions": e_out}
 
 
+def cpu_levelized(name, seed, frac):
+    """The oracle's second evaluator (levelized, OpenMP over the gates of a
+    level) on every host core, same bounded sample as cpu_baseline."""
+    import oracle
+    import synth
+    r = synth.RECIPES[name]["stim"]
+    ov = dict(stim_window=max(1, int(r["window"] * frac)), stim_mean=r["mean"] * frac)
+    if r.get("clock_trans"):
+        ov["stim_clock_trans"] = max(1, int(r["clock_trans"] * frac))
+    w = synth.make_workload(name, seed=seed, **ov)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    res = oracle.sim_levelized(w.netlist, w.stimulus, nthreads=cores)
+    dt = time.perf_counter() - t0
+    e_out = int(res.off[-1] - res.off[w.netlist.n_pi])
+    return {"value": e_out / dt, "unit": UNIT, "cores": cores, "kind": "oracle (levelized, OpenMP)",
+            "sample": f"same sample as cpu_baseline ({dt:.1f} s)", "seconds": round(dt, 2)}
+
+
 def cpu_model():
     try:
         with open("/proc/cpuinfo") as f:
@@ -391,6 +410,7 @@ def run_own(a):
     if rank == 0 and world == 1 and not a.no_cpu:
         cb = cpu_baseline(a.workload, a.seed, a.cpu_frac)
         cb["cpu"] = cpu_model()
+        cb["all_cores"] = cpu_levelized(a.workload, a.seed, a.cpu_frac)
     cfg = describe(a.workload, w)
     cfg.update({"output_transitions_per_step": e_out, "arena_words": int(arena) if arena else "default",
                 "l2_policy": "inputs larger than L2 (stimulus and intermediate waveforms >> 129 MB)",
