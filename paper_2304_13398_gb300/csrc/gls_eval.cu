@@ -343,6 +343,45 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         }
         bound += g.len[p];
     }
+    const uint32_t out_net = gr.out_net;
+
+    // state before the first input transition: pins at X, output X, nothing
+    // pending -- or, in a time slice, where the previous slice left the gate
+    uint32_t carry = 0x2Au;
+    CommitState cs{0u, kVX, 0};
+    uint32_t send = kTimeInf;   // transitions with t_r >= send stay pending
+    bool started = false;       // an input transition was evaluated (else the output is still at its X start)
+    if (r.st_in) {
+        const uint32_t h = r.st_in[out_net];
+        carry = (h & 63u) ^ 0x2Au;
+        started = (h >> 7) & 1u;
+        cs.lastV = ((h >> 8) & 3u) ^ kVX;
+        cs.np = (int)(h >> 16);
+        bound += (uint64_t)cs.np;   // each carried transition may become an output
+        send = r.slice_end;
+    }
+    if (bound == 0) {   // no input transition: the output stays as it is (X at the start, Algorithm 2)
+        if (lane == 0) {
+            r.net_ptr[out_net] = 0;
+            r.net_len[out_net] = 0;
+            if (r.st_in) r.st_out[out_net] = r.st_in[out_net];
+        }
+        return true;
+    }
+
+    // Claim the output slot and start the first window copies before the
+    // per-gate tables are built, so that the atomic's and the copies'
+    // latencies overlap that work.
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(r.arena_top, (unsigned long long)((bound + kSlotAlign - 1) & ~(uint64_t)(kSlotAlign - 1)));
+    uint32_t cur[3] = {0, 0, 0};
+    bool failed = false;
+    const int b = 0;   // the one window buffer
+    int lead[3] = {0, 0, 0}, n[3] = {0, 0, 0};
+    __syncwarp();      // the previous gate's reads of the buffer precede the copies
+    bool more = issue_windows<K, CH>(sm, 0, g, cur, lead, n, lane);
+    const bool any_input = more;
+
     g.dmin = (uint32_t)gr.dmin;
     g.lut_lo = gr.lut_lo;
     g.lut_hi = gr.lut_hi;
@@ -413,39 +452,17 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         }
         __syncwarp();
     }
-    const uint32_t out_net = gr.out_net;
-
-    // state before the first input transition: pins at X, output X, nothing
-    // pending -- or, in a time slice, where the previous slice left the gate
-    uint32_t carry = 0x2Au;
-    CommitState cs{0u, kVX, 0};
-    uint32_t send = kTimeInf;   // transitions with t_r >= send stay pending
-    bool started = false;       // an input transition was evaluated (else the output is still at its X start)
-    if (r.st_in) {
-        const uint32_t h = r.st_in[out_net];
-        carry = (h & 63u) ^ 0x2Au;
-        started = (h >> 7) & 1u;
-        cs.lastV = ((h >> 8) & 3u) ^ kVX;
-        cs.np = (int)(h >> 16);
-        bound += (uint64_t)cs.np;   // each carried transition may become an output
-        send = r.slice_end;
-    }
-    if (bound == 0) {   // no input transition: the output stays as it is (X at the start, Algorithm 2)
-        if (lane == 0) {
-            r.net_ptr[out_net] = 0;
-            r.net_len[out_net] = 0;
-            if (r.st_in) r.st_out[out_net] = r.st_in[out_net];
-        }
-        return true;
-    }
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(r.arena_top, (unsigned long long)((bound + kSlotAlign - 1) & ~(uint64_t)(kSlotAlign - 1)));
     base = __shfl_sync(FULL, base, 0);
     if (base + bound > r.arena_cap) {
         if (lane == 0) {
             atomicOr(r.status, kStArenaOverflow);
             r.net_ptr[out_net] = 0;
             r.net_len[out_net] = 0;
+        }
+        // the copies already issued land in this warp's buffer: let them finish
+        if (more && !wait_window(sm, b, par)) {
+            if (lane == 0) atomicOr(r.status, kStTimeout);
+            return false;
         }
         return true;
     }
@@ -461,13 +478,6 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
     // K == 2 uses f(a, b) with c = X (entries 32..47), K == 3 all 64
     const uint32_t lut1 = (uint32_t)(g.lut_hi >> 16) & 0xFFu;
     const uint32_t lut2 = (uint32_t)g.lut_hi;
-
-    uint32_t cur[3] = {0, 0, 0};
-    bool failed = false;
-    const int b = 0;   // the one window buffer
-    int lead[3] = {0, 0, 0}, n[3] = {0, 0, 0};
-    bool more = issue_windows<K, CH>(sm, 0, g, cur, lead, n, lane);
-    const bool any_input = more;
 
     while (more) {
         if (!wait_window(sm, b, par)) {   // the copies never completed: stop this warp
