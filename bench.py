@@ -192,9 +192,10 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str):
-    """DRAM bytes per run of the level kernel from a committed ncu summary,
-    valid only while the kernel source is unchanged."""
+def ncu_traffic(workload: str, cfg: dict):
+    """DRAM bytes per run of the gate kernel from a committed ncu summary,
+    valid only for the configuration it was taken on (sizes, seed, schedule,
+    kernel variant) and while the kernel source is unchanged."""
     p = os.path.join(ROOT, "profiles", "gate_kernel_traffic.json")
     try:
         with open(p) as f:
@@ -203,6 +204,8 @@ def ncu_traffic(workload: str):
         return None
     e = d.get(workload)
     if not e or e.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    if any(cfg.get(k) != v for k, v in e.get("applies_to", {}).items()):
         return None
     return e.get("dram_bytes_per_run")
 
@@ -398,9 +401,14 @@ def run_own(a):
                               "mirror as they go; the step ends when all waveforms and their descriptors are "
                               "in host memory (primary inputs are the caller's stimulus)"}
 
+    cfg = describe(a.workload, w)
+    cfg.update({"output_transitions_per_step": e_out, "arena_words": int(arena) if arena else "default",
+                "l2_policy": "inputs larger than L2 (stimulus and intermediate waveforms >> 129 MB)",
+                "parallelism": f"replicas{world}" if world > 1 else "single", "schedule": a.schedule, "kernel": a.kernel,
+                "gate_order": order})
     peak, peak_kind = measured_peak_gbs()
     achieved = alg_bytes / (k_ms / 1000.0) / 1e9
-    traffic = ncu_traffic(a.workload)
+    traffic = ncu_traffic(a.workload, cfg)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind,
             "kernel": (f"dependency_kernel<{a.kernel}> (one launch per run)" if a.schedule == "dependency"
@@ -411,11 +419,6 @@ def run_own(a):
         cb = cpu_baseline(a.workload, a.seed, a.cpu_frac)
         cb["cpu"] = cpu_model()
         cb["all_cores"] = cpu_levelized(a.workload, a.seed, a.cpu_frac)
-    cfg = describe(a.workload, w)
-    cfg.update({"output_transitions_per_step": e_out, "arena_words": int(arena) if arena else "default",
-                "l2_policy": "inputs larger than L2 (stimulus and intermediate waveforms >> 129 MB)",
-                "parallelism": f"replicas{world}" if world > 1 else "single", "schedule": a.schedule, "kernel": a.kernel,
-                "gate_order": order})
     launches_per_step = 1 + (1 if a.schedule == "dependency" else int(w.recipe["net"]["depth"]))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": max(a.warmup, 3), "ms_per_step": ms, "sim_time_ms": ms, "higher_is_better": True,
