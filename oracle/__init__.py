@@ -32,9 +32,13 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                          single-output cells; hand-worked edge-dependent XOR
                          example (tests/golden/edge_delay_xor.txt); a no-arc
                          entry never wins the minimum.
+The strength of these pins is itself tested: single mistakes planted in
+copies of oracle.c each fail at least one of them
+(tests/test_oracle_mutants.py).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -64,56 +68,74 @@ _lib = None
 P = ctypes.c_void_p
 
 
+def _bind(lib):
+    """Declare the C signatures on a loaded liboracle."""
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    lib.oracle_arity.restype = ctypes.c_int
+    lib.oracle_arity.argtypes = [ctypes.c_int]
+    lib.oracle_cell_bool.restype = ctypes.c_int
+    lib.oracle_cell_bool.argtypes = [ctypes.c_int] * 4
+    lib.oracle_cell_eval.restype = ctypes.c_int
+    lib.oracle_cell_eval.argtypes = [ctypes.c_int, P]
+    lib.oracle_cell_lut.restype = None
+    lib.oracle_cell_lut.argtypes = [ctypes.c_int, P]
+    lib.oracle_delay.restype = i64
+    lib.oracle_delay.argtypes = [i64, i64, ctypes.c_int]
+    lib.oracle_gate_candidates.restype = i64
+    lib.oracle_gate_candidates.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P]
+    lib.oracle_cancel_stack.restype = i64
+    lib.oracle_cancel_stack.argtypes = [i64, P, P, P, P, P]
+    lib.oracle_cancel_scan.restype = i64
+    lib.oracle_cancel_scan.argtypes = [i64, P, P, P, P]
+    lib.oracle_eval_gate.restype = i64
+    lib.oracle_eval_gate.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P, P, P]
+    lib.oracle_result_nevents.restype = i64
+    lib.oracle_result_nevents.argtypes = [P]
+    lib.oracle_result_nnets.restype = i64
+    lib.oracle_result_nnets.argtypes = [P]
+    lib.oracle_result_copy.restype = None
+    lib.oracle_result_copy.argtypes = [P, P, P, P]
+    lib.oracle_result_free.restype = None
+    lib.oracle_result_free.argtypes = [P]
+    net_args = [i32, i32, P, P, P, P, P]
+    lib.oracle_sim_levelized.restype = ctypes.c_int
+    lib.oracle_sim_levelized.argtypes = net_args + [P, P, P, ctypes.c_int, ctypes.POINTER(P)]
+    lib.oracle_sim_event.restype = ctypes.c_int
+    lib.oracle_sim_event.argtypes = net_args + [P, P, P, ctypes.POINTER(P)]
+    lib.oracle_static_eval.restype = ctypes.c_int
+    lib.oracle_static_eval.argtypes = [i32, i32, P, P, P, P, P]
+    lib.oracle_check_gates.restype = i64
+    lib.oracle_check_gates.argtypes = net_args + [P, P, P, i32, i32, ctypes.c_int, ctypes.POINTER(i64)]
+    lib.oracle_edge_class.restype = ctypes.c_int
+    lib.oracle_edge_class.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.oracle_arc_delay4.restype = i64
+    lib.oracle_arc_delay4.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    lib.oracle_cell_candidates.restype = i64
+    lib.oracle_cell_candidates.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P]
+    lib.oracle_sim_cells.restype = ctypes.c_int
+    lib.oracle_sim_cells.argtypes = [i32, i32, P, P, P, P, P, P, P, P, P, P, ctypes.POINTER(P)]
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        i32, i64 = ctypes.c_int32, ctypes.c_int64
-        lib.oracle_arity.restype = ctypes.c_int
-        lib.oracle_arity.argtypes = [ctypes.c_int]
-        lib.oracle_cell_bool.restype = ctypes.c_int
-        lib.oracle_cell_bool.argtypes = [ctypes.c_int] * 4
-        lib.oracle_cell_eval.restype = ctypes.c_int
-        lib.oracle_cell_eval.argtypes = [ctypes.c_int, P]
-        lib.oracle_cell_lut.restype = None
-        lib.oracle_cell_lut.argtypes = [ctypes.c_int, P]
-        lib.oracle_delay.restype = i64
-        lib.oracle_delay.argtypes = [i64, i64, ctypes.c_int]
-        lib.oracle_gate_candidates.restype = i64
-        lib.oracle_gate_candidates.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P]
-        lib.oracle_cancel_stack.restype = i64
-        lib.oracle_cancel_stack.argtypes = [i64, P, P, P, P, P]
-        lib.oracle_cancel_scan.restype = i64
-        lib.oracle_cancel_scan.argtypes = [i64, P, P, P, P]
-        lib.oracle_eval_gate.restype = i64
-        lib.oracle_eval_gate.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P, P, P]
-        lib.oracle_result_nevents.restype = i64
-        lib.oracle_result_nevents.argtypes = [P]
-        lib.oracle_result_nnets.restype = i64
-        lib.oracle_result_nnets.argtypes = [P]
-        lib.oracle_result_copy.restype = None
-        lib.oracle_result_copy.argtypes = [P, P, P, P]
-        lib.oracle_result_free.restype = None
-        lib.oracle_result_free.argtypes = [P]
-        net_args = [i32, i32, P, P, P, P, P]
-        lib.oracle_sim_levelized.restype = ctypes.c_int
-        lib.oracle_sim_levelized.argtypes = net_args + [P, P, P, ctypes.c_int, ctypes.POINTER(P)]
-        lib.oracle_sim_event.restype = ctypes.c_int
-        lib.oracle_sim_event.argtypes = net_args + [P, P, P, ctypes.POINTER(P)]
-        lib.oracle_static_eval.restype = ctypes.c_int
-        lib.oracle_static_eval.argtypes = [i32, i32, P, P, P, P, P]
-        lib.oracle_check_gates.restype = i64
-        lib.oracle_check_gates.argtypes = net_args + [P, P, P, i32, i32, ctypes.c_int, ctypes.POINTER(i64)]
-        lib.oracle_edge_class.restype = ctypes.c_int
-        lib.oracle_edge_class.argtypes = [ctypes.c_int, ctypes.c_int]
-        lib.oracle_arc_delay4.restype = i64
-        lib.oracle_arc_delay4.argtypes = [P, ctypes.c_int, ctypes.c_int]
-        lib.oracle_cell_candidates.restype = i64
-        lib.oracle_cell_candidates.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P]
-        lib.oracle_sim_cells.restype = ctypes.c_int
-        lib.oracle_sim_cells.argtypes = [i32, i32, P, P, P, P, P, P, P, P, P, P, ctypes.POINTER(P)]
-        _lib = lib
+        _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+@contextlib.contextmanager
+def library(path: str):
+    """Run the oracle's functions on another build of oracle.c (a copy with a
+    planted mistake, in the tests that check the pins catch it) for the
+    duration of the block."""
+    global _lib
+    prev = _lib
+    _lib = _bind(ctypes.CDLL(os.path.abspath(path)))
+    try:
+        yield
+    finally:
+        _lib = prev
 
 
 def _p(a: np.ndarray):
