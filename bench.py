@@ -121,7 +121,8 @@ def describe(name, w):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 25 ms (a timed
+    region of ten 1M-gate runs lasts about 180 ms)."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -130,17 +131,25 @@ class ClockSampler:
         self.idx = gpu_index
         self.proc = None
         self.lines = []
+        self.m = 0
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()   # let the sampler start before the timed region
+            while not self.lines and self.proc.poll() is None and time.time() - t0 < 3.0:
+                time.sleep(0.02)
         except OSError:
             self.proc = None
         return self
+
+    def mark(self):
+        """Start of the timed region: summary() uses the samples after it."""
+        self.m = len(self.lines)
 
     def _read(self):
         for ln in self.proc.stdout:
@@ -157,7 +166,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.m:]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 8:
                 continue
@@ -259,15 +268,28 @@ def cpu_levelized(name, seed, frac):
             "sample": f"same sample as cpu_baseline ({dt:.1f} s)", "seconds": round(dt, 2)}
 
 
+# Arm "CPU part" numbers of the Neoverse cores found in Grace-class hosts
+ARM_PARTS = {"0xd40": "Neoverse-V1", "0xd4f": "Neoverse-V2", "0xd84": "Neoverse-V3", "0xd0c": "Neoverse-N1",
+             "0xd49": "Neoverse-N2"}
+
+
 def cpu_model():
+    """Host CPU model: the x86 model name, or the Arm core by part number."""
     try:
         with open("/proc/cpuinfo") as f:
             for ln in f:
-                if ln.lower().startswith(("model name", "cpu part")):
-                    return ln.split(":", 1)[1].strip()
+                key, _, val = ln.partition(":")
+                key, val = key.strip().lower(), val.strip()
+                if key == "model name":
+                    return val
+                if key == "cpu part":
+                    return f"{ARM_PARTS.get(val.lower(), 'Arm core')} (CPU part {val}, {os.uname().machine})"
     except OSError:
         pass
     return os.uname().machine
+
+
+REF_RUN_SECONDS = 120.0   # oracle time of all timed steps of the reference arm together
 
 
 def run_reference(a):
@@ -277,11 +299,17 @@ def run_reference(a):
     import synth
     w = synth.make_workload(a.workload, seed=a.seed, **overrides(a))
     cfg = describe(a.workload, w)
-    for _ in range(a.warmup):
-        cpu_baseline(a.workload, a.seed, a.cpu_frac / 4)
+    # the untimed warm-up samples (a quarter of the default size) also give
+    # the oracle's pace, from which every timed step's sample is sized so
+    # that all K of them take about REF_RUN_SECONDS together
+    fw = a.cpu_frac / 4
+    pace = 0.0
+    for _ in range(max(a.warmup, 1)):
+        pace = cpu_baseline(a.workload, a.seed, fw)["seconds"] / fw
+    frac = min(a.cpu_frac, REF_RUN_SECONDS / max(1, a.steps) / max(pace, 1e-9))
     vals, secs = [], []
     for _ in range(a.steps):
-        b = cpu_baseline(a.workload, a.seed, a.cpu_frac)
+        b = cpu_baseline(a.workload, a.seed, frac)
         vals.append(b["value"])
         secs.append(b["seconds"])
     v = statistics.median(vals)
@@ -289,7 +317,7 @@ def run_reference(a):
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": 1000 * statistics.median(secs), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": cfg,
         "cpu_baseline": cb,
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
     return 0
@@ -345,6 +373,7 @@ def run_own(a):
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kernel_ms = []
     with ClockSampler(local) as clk:
+        clk.mark()
         start.record(stream)
         for _ in range(a.steps):
             ctx.rerun(rid, stream)
@@ -405,7 +434,8 @@ def run_own(a):
     cfg.update({"output_transitions_per_step": e_out, "arena_words": int(arena) if arena else "default",
                 "l2_policy": "inputs larger than L2 (stimulus and intermediate waveforms >> 129 MB)",
                 "parallelism": f"replicas{world}" if world > 1 else "single", "schedule": a.schedule, "kernel": a.kernel,
-                "gate_order": order})
+                "gate_order": order,
+                "event_format": "packed u32 transitions (t << 2) | v: 30-bit time, 2-bit value 0/1/X/Z"})
     peak, peak_kind = measured_peak_gbs()
     achieved = alg_bytes / (k_ms / 1000.0) / 1e9
     traffic = ncu_traffic(a.workload, cfg)
@@ -422,7 +452,7 @@ def run_own(a):
     launches_per_step = 1 + (1 if a.schedule == "dependency" else int(w.recipe["net"]["depth"]))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": max(a.warmup, 3), "ms_per_step": ms, "sim_time_ms": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32 packed events (int32 time, 2-bit value)",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
             "gpu_launches": launches_per_step * a.steps, "clocks": clk.summary()}
     if rank == 0:
@@ -566,7 +596,7 @@ def run_batch(a):
             "speedup_vs_plain": (b_tr / b_ms) / (p_tr / p_ms), "items_match_plain": b_tr == p_tr,
             "gate_order_1m": order, "wave_size": wave, "waves": waves, "autotune": {"best": tune.best,
                                                              "trials": [[c, m] for c, m in tune.timings_ms]},
-            "data": "synthetic", "dtype": "u32 packed events"}
+            "data": "synthetic", "dtype": "u32"}
     print(json.dumps(line))
     return 0
 
@@ -638,7 +668,7 @@ def run_sliced(a):
             "mode": "sliced", "n_gpus": 1, "higher_is_better": True, "kernel": a.kernel, "gate_order": order,
             "unsliced": {"transitions": plain.total_events, "device_ms": plain.kernel_ms,
                          "value": plain.total_events / (plain.kernel_ms / 1000.0)},
-            **out, "data": "synthetic", "dtype": "u32 packed slice-local events, 64-bit slice origins"}
+            **out, "data": "synthetic", "dtype": "u32"}
     print(json.dumps(line))
     return 0
 
@@ -687,7 +717,7 @@ def run_serve(a):
             "mode": "serve", "served": out["served"], "served_fifo": out["served_fifo"], "plain": out["plain"],
             "netlists": [int(x) for x in sizes], "budget_bytes": budget,
             "latency": "request arrival -> its waveforms resident on the device",
-            "data": "synthetic", "dtype": "u32 packed events"}
+            "data": "synthetic", "dtype": "u32"}
     print(json.dumps(line))
     return 0
 
