@@ -74,8 +74,13 @@ class ServeStats:
 
 class Server:
     def __init__(self, ctx: Context, budget_bytes: int, max_batch: int = 16, streams: int = 4,
-                 batching: bool = True, safety: float = 1.3, keep_results: bool = False, policy: str = "sjf"):
-        import torch
+                 batching: bool = True, safety: float = 1.3, keep_results: bool = False, policy: str = "sjf",
+                 stream_factory=None):
+        """stream_factory() makes one launch stream (default: a new CUDA
+        stream); the dispatcher only hands the streams to the context."""
+        if stream_factory is None:
+            import torch
+            stream_factory = torch.cuda.Stream
         self.ctx = ctx
         self.budget = int(budget_bytes)
         self.max_batch = max_batch if batching else 1
@@ -84,7 +89,7 @@ class Server:
         if policy not in ("sjf", "fifo"):
             raise ValueError(policy)
         self.policy = policy
-        self.streams = [torch.cuda.Stream() for _ in range(max(1, streams))]
+        self.streams = [stream_factory() for _ in range(max(1, streams))]
         self.res: dict[str, Resident] = {}
 
     # ---- resident netlists ----
