@@ -125,8 +125,9 @@ const char *gls_last_error(gls_ctx *ctx);
 
 /*
  * Validate (as gls_check_netlist), levelize and copy a netlist to the device:
- * gates are reordered by level into a structure-of-arrays record per gate;
- * the device copy is immutable.  *netlist_id receives a handle.
+ * gates are reordered by level, one 64-byte record per gate (fanin net ids,
+ * delays, the cell's 4-value table); the device copy is immutable.
+ * *netlist_id receives a handle.
  */
 int gls_load_netlist(gls_ctx *ctx, int32_t n_pi, int32_t n_gates, const uint8_t *type,
                      const int32_t *fanin_off, const int32_t *fanin_net, const int32_t *d_rise,
@@ -155,7 +156,8 @@ int gls_update_stimulus(gls_ctx *ctx, int32_t stim_id, const int64_t *off, const
  * Simulate a netlist under a stimulus: allocate the run's waveform store
  * (net descriptors plus an event arena of arena_events 32-bit words; 0 means
  * 256 words per stimulus transition plus 2^20, capped at half of the unused
- * budget) and enqueue the whole level-by-level evaluation as one
+ * budget) and enqueue the whole evaluation (one persistent launch with the
+ * dependency schedule, one launch per level with the level schedule) as one
  * CUDA graph on cuda_stream (a cudaStream_t; NULL = the context's stream).
  * Stream-ordered: returns once the work is enqueued.  The result stays on the
  * device until gls_release.  GLS_ERANGE if a time could reach 2^30.
@@ -400,7 +402,8 @@ enum { GLS_KERNEL_SEGMENTED = 0, GLS_KERNEL_WINDOWED = 1, GLS_KERNEL_WINDOWED_WI
    LEVELS: one kernel launch per DAG level (the topological-layer partition
    the paper criticises, kept as the reference form), all in one CUDA graph.
    DEPENDENCY: one persistent launch; each warp takes the next gate in level
-   order and starts it as soon as its fanin gates are done (Algorithm 1's
+   order (or the netlist's planned order, gls_plan_order) and starts it as
+   soon as its fanin gates are done (Algorithm 1's
    readiness test, without layer barriers); a wait longer than
    GLS_OPT_WAIT_LIMIT_MS ends the run with GLS_ETIMEOUT. */
 enum { GLS_SCHEDULE_LEVELS = 0, GLS_SCHEDULE_DEPENDENCY = 1 };
