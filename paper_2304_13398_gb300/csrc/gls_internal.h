@@ -99,8 +99,8 @@ constexpr int kPendCap = 256;
 // gate on another SM writes later in the same launch).
 constexpr uint32_t kSlotAlign = 32;   // words
 
-// Gate kernel variants: warp-wide shared-memory windows of 128 (default) or
-// 256 transitions per pin, or per-lane time segments.
+// Gate kernel variants: warp-wide shared-memory windows of 128 or 352
+// (default) transitions per pin of 3-input cells, or per-lane time segments.
 enum { kVariantSegmented = 0, kVariantWindowed = 1, kVariantWindowedWide = 2 };
 
 // Launch configuration of the gate kernels.
