@@ -142,3 +142,23 @@ def test_x_start_and_no_event_gate():
     # X <-> Z changes on an input do not change the cell value
     t, v = oracle.eval_gate(oracle.BUF, [([1, 2, 3, 4], [1, Z, X, 0])], [2], [5])
     assert list(zip(t.tolist(), v.tolist())) == [(3, 1), (4, X), (9, 0)]
+
+
+def test_eq1_random_long_sequences():
+    """Beyond the exhaustive short cases: long random candidate sequences
+    (many ties, deep cancellation chains) give the same waveform in the
+    stack form, the scan form and the value-function characterisation."""
+    rng = np.random.default_rng(11)
+    for trial in range(300):
+        n = int(rng.integers(6, 60))
+        trs = rng.integers(0, max(2, n // 2), size=n).tolist()
+        vs, prev = [], X
+        for _ in range(n):
+            v = int(rng.choice([x for x in (0, 1, X) if x != prev]))
+            vs.append(v)
+            prev = v
+        want = _wave_from_value_function(trs, vs, -1, max(trs) + 1)
+        t1, v1 = oracle.cancel_stack(list(range(n)), trs, vs)
+        t2, v2 = oracle.cancel_scan(trs, vs)
+        assert list(zip(t1.tolist(), v1.tolist())) == want, (trs, vs)
+        assert list(zip(t2.tolist(), v2.tolist())) == want, (trs, vs)
