@@ -162,3 +162,45 @@ def test_time_translation_beyond_32_bits():
         np.testing.assert_array_equal(base.t + D, far.t)
         np.testing.assert_array_equal(base.v, far.v)
     assert oracle.check_gates(nl, far.off, far.t, far.v) == (0, -1)
+
+
+def test_same_net_on_both_pins_closed_forms():
+    """One net on both pins of a cell: both pins change at the same time, so
+    the delay is the smaller of the two arcs (Sec. 2.3, all changed pins),
+    and each pin's X is completed on its own (Sec. 2.2).  AND2(a, a) is then
+    a with Z read as X, shifted by min(d0, d1); XOR2(a, a) is 0 while a is
+    0 or 1 and X while it is X or Z, shifted by the arc delay."""
+    from synth import Netlist
+    rng = np.random.default_rng(21)
+    for trial in range(60):
+        d0, d1, dx = (int(x) for x in rng.integers(1, 25, size=3))
+        typ = np.array([oracle.AND2, oracle.XOR2], np.uint8)
+        off = np.array([0, 2, 4], np.int32)
+        net = np.zeros(4, np.int32)                       # every pin reads PI 0
+        dly = np.array([d0, d1, dx, dx], np.int32)
+        nl = Netlist(1, typ, off, net, dly, dly.copy())
+        n = int(rng.integers(0, 25))
+        ts = np.sort(rng.choice(np.arange(0, 400), size=n, replace=False)).astype(np.int32)
+        vs, prev = [], X
+        for _ in range(n):
+            v = int(rng.choice([x for x in (0, 1, X, Z) if x != prev]))
+            vs.append(v)
+            prev = v
+        st = synth.Stimulus(np.array([0, n], np.int64), ts, np.array(vs, np.uint8))
+
+        def shifted(f, d):
+            out, last = [], X
+            for t, v in zip(ts.tolist(), vs):
+                y = f(v)
+                if y != last:
+                    out.append((t + d, y))
+                    last = y
+            return out
+
+        want_and = shifted(lambda v: X if v == Z else v, min(d0, d1))
+        want_xor = shifted(lambda v: 0 if v in (0, 1) else X, dx)
+        for sim in (oracle.sim_event, oracle.sim_levelized):
+            r = sim(nl, st)
+            for g, want in ((0, want_and), (1, want_xor)):
+                t, v = r.net(1 + g)
+                assert list(zip(t.tolist(), v.tolist())) == want, (g, ts, vs, d0, d1, dx)
