@@ -17,7 +17,10 @@ resident stimulus.  The dispatcher:
 Device buffers come from the context's pool, so admitting and retiring never
 synchronises the device.  policy="sjf" admits the waiting request with the
 least estimated work first (shortest job first: small windows do not queue
-behind large ones); "fifo" admits in arrival order.  batching=False,
+behind large ones); "fifo" admits in arrival order.  With max_wait_s, a
+request that has waited longer than that is admitted before any shorter one
+(oldest first), which bounds how long shortest-first can hold a large
+request back.  batching=False,
 streams=1, policy="fifo" gives the plain form: one request per launch, one
 launch at a time, in arrival order.
 """
@@ -75,7 +78,7 @@ class ServeStats:
 class Server:
     def __init__(self, ctx: Context, budget_bytes: int, max_batch: int = 16, streams: int = 4,
                  batching: bool = True, safety: float = 1.3, keep_results: bool = False, policy: str = "sjf",
-                 stream_factory=None):
+                 stream_factory=None, max_wait_s: float | None = None):
         """stream_factory() makes one launch stream (default: a new CUDA
         stream); the dispatcher only hands the streams to the context."""
         if stream_factory is None:
@@ -89,6 +92,7 @@ class Server:
         if policy not in ("sjf", "fifo"):
             raise ValueError(policy)
         self.policy = policy
+        self.max_wait_s = max_wait_s
         self.streams = [stream_factory() for _ in range(max(1, streams))]
         self.res: dict[str, Resident] = {}
 
@@ -193,7 +197,12 @@ class Server:
                 with lock:
                     if not pending:
                         break
-                    if self.policy == "sjf":
+                    now_s = time.perf_counter() - t0
+                    overdue = [] if self.max_wait_s is None else \
+                        [q for q in pending if now_s - q.arrival > self.max_wait_s]
+                    if overdue:
+                        head = min(overdue, key=lambda q: q.arrival)
+                    elif self.policy == "sjf":
                         head = min(pending, key=lambda q: self.estimate_words(q.netlist, q.t_limit))
                     else:
                         head = pending[0]

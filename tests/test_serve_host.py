@@ -117,6 +117,21 @@ def test_shortest_job_first():
     assert order[1:] == sorted(windows[1:]) if order[0] == 5000 else order == sorted(windows)
 
 
+def test_aging_bounds_how_long_shortest_first_holds_a_large_request():
+    def order(max_wait_s):
+        ctx = FakeCtx({1: 1.0}, polls=400)   # each launch holds the one stream for >= 20 ms
+        srv = make_server(ctx, [1], budget_bytes=1 << 40, batching=False, streams=1, policy="sjf",
+                          max_wait_s=max_wait_s)
+        reqs = [Request(0, "n1", 5000, 0.0), Request(1, "n1", 9000, 0.001)]
+        reqs += [Request(2 + i, "n1", 100 + i, 0.0015 + 0.0001 * i) for i in range(4)]
+        srv.serve(reqs)
+        return [l[1][0] for l in ctx.launches]
+
+    assert order(None)[-1] == 9000            # pure shortest-first: the large request goes last
+    aged = order(0.005)                       # waited past 5 ms: oldest first
+    assert aged[:2] == [5000, 9000] and aged[2:] == [100, 101, 102, 103]
+
+
 def test_batches_hold_one_netlist_and_respect_max_batch():
     ctx = FakeCtx({1: 1.0, 2: 1.0}, polls=50)
     srv = make_server(ctx, [1, 2], budget_bytes=1 << 40, max_batch=3, streams=2)
