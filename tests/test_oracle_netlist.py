@@ -204,3 +204,25 @@ def test_same_net_on_both_pins_closed_forms():
             for g, want in ((0, want_and), (1, want_xor)):
                 t, v = r.net(1 + g)
                 assert list(zip(t.tolist(), v.tolist())) == want, (g, ts, vs, d0, d1, dx)
+
+
+def test_event_driven_equals_levelized_fuzz():
+    """The two independent simulators on many tiny random netlists with
+    extreme settings: unit or wide delay ranges, dense pulses, X/Z-heavy
+    stimuli, single cell types and shuffled gate numbering."""
+    rng = np.random.default_rng(2024)
+    for trial in range(400):
+        n_pi = int(rng.integers(1, 4))
+        depth = int(rng.integers(1, 5))
+        G = int(rng.integers(depth, 12))
+        d_min = int(rng.integers(1, 4))
+        d_max = d_min + int(rng.choice([0, 1, 3, 40]))
+        cells = int(rng.choice([synth.ALL_CELLS, 1 << int(rng.integers(0, 11)), int(rng.integers(1, synth.ALL_CELLS + 1))]))
+        nl = synth.make_netlist(n_pi, G, depth, fanout="geometric" if trial % 2 else "pareto", d_min=d_min,
+                                d_max=d_max, cells=cells, seed=1000 + trial, shuffle=bool(trial % 3 == 0))
+        probs = [(0.45, 0.45, 0.07, 0.03), (0.25, 0.25, 0.25, 0.25), (0.5, 0.5, 0.0, 0.0)][trial % 3]
+        st = synth.make_stimulus(n_pi, mean=float(rng.integers(1, 30)), window=int(rng.integers(5, 80)),
+                                 probs=probs, seed=2000 + trial)
+        a = oracle.sim_event(nl, st)
+        b = oracle.sim_levelized(nl, st)
+        assert np.array_equal(a.off, b.off) and np.array_equal(a.t, b.t) and np.array_equal(a.v, b.v), trial
