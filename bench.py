@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve", "sliced"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve", "sliced", "cells"],
                     help="plain: one 1M-gate run (the headline); batch: 64 stimulus sets + 16 netlists "
                          "in batched launches vs one at a time; serve: 200 req/s over resident netlists, "
                          "continuous batching vs plain")
@@ -673,6 +673,71 @@ def run_sliced(a):
     return 0
 
 
+def run_cells(a):
+    """General cells at the benchmark's size (the full delay matrix with its
+    input-edge dimension, multi-output cells and user tables, Sec. 3): the
+    workload's netlist structure with every cell a user cell drawn from a
+    shared library (64 prototype tables per input count and output), 30%
+    two-output cells, edge-dependent delays on half the outputs and 10% of
+    the (pin, output) pairs without an arc, under the workload's stimulus.
+    Gate-kernel device time (CUDA events, median of --steps reruns after 3
+    warm-ups) against the built-in-cell netlist of the same structure in the
+    same context, both in level order."""
+    import torch
+    import paper_2304_13398_gb300 as gls
+    import synth
+    torch.cuda.set_device(0)
+    w = synth.make_workload(a.workload, seed=a.seed)
+    net = w.recipe["net"]
+    cn = synth.make_cell_netlist(net["n_pi"], net["n_gates"], net["depth"], seed=a.seed, fanout=net["fanout"],
+                                 d_min=net["d_min"], d_max=net["d_max"], multi_frac=0.3, edge_frac=0.5,
+                                 noarc_frac=0.1, x_frac=0.6, library=64)
+    ctx = gls.Context(0)
+    ctx.set_kernel(a.kernel)
+
+    def timed(nid, sid):
+        rid = ctx.simulate(nid, sid)
+        rc, demand, _ = ctx.run_stats_raw(rid)
+        while rc == gls.gls.GLS_EOVERFLOW:
+            ctx.release(rid)
+            rid = ctx.simulate(nid, sid, arena_events=int(demand * 1.25) + 1024)
+            rc, demand, _ = ctx.run_stats_raw(rid)
+        if rc != 0:
+            raise gls.GlsError(rc, "cells run failed")
+        for _ in range(3):
+            ctx.rerun(rid)
+        ms = []
+        for _ in range(a.steps):
+            ctx.rerun(rid)
+            ms.append(ctx.run_stats(rid).kernel_ms)
+        total = ctx.run_stats(rid).total_events
+        ctx.release(rid)
+        k_ms = statistics.median(ms)
+        return {"transitions": total, "device_ms": k_ms, "value": total / (k_ms / 1000.0)}
+
+    sid = ctx.load_stimulus(w.stimulus)
+    cid = ctx.load_cell_netlist_shared(cn)
+    cells = timed(cid, sid)
+    ctx.release(cid)
+    bid = ctx.load_netlist(w.netlist)
+    builtin = timed(bid, sid)
+    ctx.close()
+    k = np.diff(cn.fanin_off)
+    line = {"metric": "general-cell output transitions/s (1M cells: shared user tables, edge-dependent delays, "
+                      "two-output cells, pins without arcs)", "unit": UNIT, "mode": "cells", "n_gpus": 1,
+            "higher_is_better": True, "kernel": a.kernel, "schedule": "dependency", "gate_order": "level",
+            "steps": a.steps, "warmup": 3,
+            "cells": dict(cells, cells=int(cn.n_cells), output_records=int(cn.n_out.sum()),
+                          two_output_cells=int((cn.n_out == 2).sum()),
+                          edge_dependent_outputs="about half", no_arc_pairs="about 10% of multi-input pairs",
+                          library_tables=64, mean_inputs=float(k.mean())),
+            "builtin": dict(builtin, gates=int(w.netlist.n_gates)),
+            "device_time_ratio": cells["device_ms"] / builtin["device_ms"],
+            "config": describe(a.workload, w), "data": "synthetic", "dtype": "u32"}
+    print(json.dumps(line))
+    return 0
+
+
 def run_serve(a):
     """Served form: a seeded Poisson request stream (200 req/s, 30 s) over 8
     resident netlists of log-uniform size (5k-5M gates), stimulus windows
@@ -732,6 +797,8 @@ def main():
         return run_serve(a)
     if a.mode == "sliced":
         return run_sliced(a)
+    if a.mode == "cells":
+        return run_cells(a)
     return run_own(a)
 
 

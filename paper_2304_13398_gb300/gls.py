@@ -246,6 +246,20 @@ class Context:
             types[c] = self.define_cell(cn.n_in(c), cn.luts[cn.lut_off[c]:cn.lut_off[c + 1]])
         return self.load_netlist_cells(cn.n_pi, types, cn.fanin_off, cn.fanin_net, cn.delays)
 
+    def load_cell_netlist_shared(self, cn) -> int:
+        """Load a CellNetlist, defining each distinct cell (input count and
+        tables of all its outputs) once and sharing it between instances."""
+        lib: dict = {}
+        types = np.zeros(cn.n_cells, np.int32)
+        for c in range(cn.n_cells):
+            tab = cn.luts[cn.lut_off[c]:cn.lut_off[c + 1]]
+            key = (cn.n_in(c), tab.tobytes())
+            t = lib.get(key)
+            if t is None:
+                t = lib[key] = self.define_cell(cn.n_in(c), tab)
+            types[c] = t
+        return self.load_netlist_cells(cn.n_pi, types, cn.fanin_off, cn.fanin_net, cn.delays)
+
     def load_stimulus64(self, st, n_pi: int | None = None) -> int:
         """A stimulus with 64-bit times (for simulate_sliced)."""
         off, t, v = _c(st.off, np.int64), _c(st.t, np.int64), _c(st.v, np.uint8)

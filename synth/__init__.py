@@ -178,7 +178,8 @@ class CellNetlist:
 
 def make_cell_netlist(n_pi: int, n_cells: int, depth: int, *, seed: int = 1, multi_frac: float = 0.3,
                       edge_frac: float = 0.5, noarc_frac: float = 0.1, x_frac: float = 0.6, d_min: int = 5,
-                      d_max: int = 200, fanout: str = "pareto", shuffle: bool = False) -> CellNetlist:
+                      d_max: int = 200, fanout: str = "pareto", shuffle: bool = False,
+                      library: int = 0) -> CellNetlist:
     """Seeded general-cell netlist on the structure of make_netlist: each cell
     has 1 or 2 outputs (multi_frac), user tables drawn at random (0/1 inputs
     give a random 0/1; inputs with X/Z give X with probability x_frac, else a
@@ -186,7 +187,10 @@ def make_cell_netlist(n_pi: int, n_cells: int, depth: int, *, seed: int = 1, mul
     edge for a fraction edge_frac of the outputs, and, for a fraction
     noarc_frac of (pin, output) pairs of multi-input cells, no arc -- the
     output's table is then made independent of that pin.  About half of the
-    reads of a 2-output cell use its second output."""
+    reads of a 2-output cell use its second output.  With library > 0 the
+    tables and the pins without an arc come from `library` prototype cells
+    per input count and output (a cell library shared by many instances);
+    the delays stay per instance."""
     base = make_netlist(n_pi, n_cells, depth, fanout=fanout, d_min=d_min, d_max=d_max, seed=seed, shuffle=shuffle)
     rng = np.random.default_rng(seed * 7919 + 17)
     C = base.n_gates
@@ -222,13 +226,17 @@ def make_cell_netlist(n_pi: int, n_cells: int, depth: int, *, seed: int = 1, mul
             cs = cells[n_out[cells] > o]
             if len(cs) == 0:
                 continue
-            T = rng.integers(0, 2, (len(cs), n4)).astype(np.uint8)
-            xs = (rng.random((len(cs), n4)) < x_frac) & ~all01
-            T[xs] = 2
-            D = rng.integers(d_min, d_max + 1, (len(cs), kk, 2, 2)).astype(np.int32)
-            same = rng.random(len(cs)) >= edge_frac
-            D[same, :, 1, :] = D[same, :, 0, :]
-            if kk > 1:
+            if library > 0:
+                T, D = _library_tables(rng, library, cs, kk, n4, idx, all01, x_frac, noarc_frac, edge_frac,
+                                       d_min, d_max)
+            else:
+                T = rng.integers(0, 2, (len(cs), n4)).astype(np.uint8)
+                xs = (rng.random((len(cs), n4)) < x_frac) & ~all01
+                T[xs] = 2
+                D = rng.integers(d_min, d_max + 1, (len(cs), kk, 2, 2)).astype(np.int32)
+                same = rng.random(len(cs)) >= edge_frac
+                D[same, :, 1, :] = D[same, :, 0, :]
+            if kk > 1 and library == 0:
                 noarc = rng.random((len(cs), kk)) < noarc_frac
                 noarc[noarc.all(axis=1), 0] = False          # keep at least one arc
                 for p in range(kk):
@@ -247,6 +255,28 @@ def make_cell_netlist(n_pi: int, n_cells: int, depth: int, *, seed: int = 1, mul
                         at = delay_off[cs] + ((p * n_out[cs] + o) * 2 + e) * 2 + v
                         delays[at] = D[:, p, e, v]
     return CellNetlist(n_pi, n_out, base.fanin_off.astype(np.int32), fanin_net, luts, lut_off, delays, delay_off)
+
+
+def _library_tables(rng, library, cs, kk, n4, idx, all01, x_frac, noarc_frac, edge_frac, d_min, d_max):
+    """Tables of `library` prototypes (pins without an arc made irrelevant to
+    the table), one drawn per cell, and per-instance delays with -1 for the
+    prototype's pins without an arc."""
+    T = rng.integers(0, 2, (library, n4)).astype(np.uint8)
+    T[(rng.random((library, n4)) < x_frac) & ~all01] = 2
+    noarc = np.zeros((library, kk), bool)
+    if kk > 1:
+        noarc = rng.random((library, kk)) < noarc_frac
+        noarc[noarc.all(axis=1), 0] = False
+        for p in range(kk):
+            rows = np.nonzero(noarc[:, p])[0]
+            if len(rows):
+                T[rows] = T[rows][:, idx & ~(3 << (2 * p))]
+    pick = rng.integers(0, library, len(cs))
+    D = rng.integers(d_min, d_max + 1, (len(cs), kk, 2, 2)).astype(np.int32)
+    same = rng.random(len(cs)) >= edge_frac
+    D[same, :, 1, :] = D[same, :, 0, :]
+    D[noarc[pick]] = -1
+    return T[pick], D
 
 
 @dataclass

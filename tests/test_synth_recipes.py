@@ -93,3 +93,26 @@ def test_ind1m_benchmark_figures():
     assert round(st.wcv(), 3) == 0.022
     c = np.diff(st.off)
     assert abs(c.mean() - 2000) < 5
+
+
+def test_cell_library_option():
+    """Shared cell library: tables come from a few prototypes and a pin
+    without an arc (all four delays -1) never matters to its output's table;
+    without the option every instance draws its own tables."""
+    cn = synth.make_cell_netlist(8, 3000, 9, seed=8, library=16, noarc_frac=0.2)
+    k = np.diff(cn.fanin_off)
+    sets = {(int(k[c]), cn.luts[cn.lut_off[c]:cn.lut_off[c + 1]].tobytes()) for c in range(cn.n_cells)}
+    assert len(sets) <= 3 * (16 + 16 * 16)
+    for c in range(0, cn.n_cells, 7):
+        kk, no = int(k[c]), int(cn.n_out[c])
+        n4 = 4 ** kk
+        for o in range(no):
+            tab = cn.luts[cn.lut_off[c] + o * n4: cn.lut_off[c] + (o + 1) * n4]
+            for p in range(kk):
+                d = cn.delays[cn.delay_off[c] + (p * no + o) * 4: cn.delay_off[c] + (p * no + o) * 4 + 4]
+                assert np.all(d == -1) or np.all(d >= 5)
+                if np.all(d == -1):
+                    idx = np.arange(n4)
+                    assert np.array_equal(tab, tab[idx & ~(3 << (2 * p))])
+    plain = synth.make_cell_netlist(8, 300, 6, seed=3)
+    assert len({plain.luts[plain.lut_off[c]:plain.lut_off[c + 1]].tobytes() for c in range(plain.n_cells)}) > 250
