@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve", "sliced", "cells"],
                     help="plain: one 1M-gate run (the headline); batch: 64 stimulus sets + 16 netlists "
                          "in batched launches vs one at a time; serve: 200 req/s over resident netlists, "
-                         "continuous batching vs plain")
+                         "continuous batching vs plain; sliced: time slices and a 2.97e9 ps stimulus; "
+                         "cells: 1M general cells vs built-in cells")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--batch-sets", type=int, default=64)
