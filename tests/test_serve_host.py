@@ -119,7 +119,7 @@ def test_shortest_job_first():
 
 def test_aging_bounds_how_long_shortest_first_holds_a_large_request():
     def order(max_wait_s):
-        ctx = FakeCtx({1: 1.0}, polls=400)   # each launch holds the one stream for >= 20 ms
+        ctx = FakeCtx({1: 1.0}, polls=2000)  # each launch holds the one stream for >= 100 ms
         srv = make_server(ctx, [1], budget_bytes=1 << 40, batching=False, streams=1, policy="sjf",
                           max_wait_s=max_wait_s)
         reqs = [Request(0, "n1", 5000, 0.0), Request(1, "n1", 9000, 0.001)]
