@@ -172,3 +172,57 @@ def test_general_invariants():
         assert np.all(v <= 2)
         if len(v):
             assert v[0] != X and np.all(v[1:] != v[:-1])
+
+
+def test_cell_candidates_against_time_stepping():
+    """Algorithm 2 for general cells against a time-stepped brute force on
+    random user tables, edge-dependent delays and pins without arcs: at every
+    integer time the pins with a transition there are applied together, the
+    table gives the new value, and a change takes the smallest delay entry
+    over those pins' arcs for their edge class (read from the hand-listed
+    classes of tests/golden/edge_classes.txt; neither edge: both) toward the
+    new value (X: both values), or the output's fastest arc toward it when
+    none of them has an arc."""
+    cls = {}
+    for ln in _lines("edge_classes.txt"):
+        o, n, c = ln.split()
+        cls[(SYM[o], SYM[n])] = {"R": (0,), "F": (1,), "N": (0, 1)}[c]
+    rng = np.random.default_rng(17)
+    for trial in range(300):
+        k = int(rng.integers(1, 4))
+        n4 = 4 ** k
+        lut = rng.integers(0, 3, n4).astype(np.uint8)
+        D = rng.integers(1, 30, (k, 2, 2)).astype(np.int64)
+        for p in range(1, k):
+            if rng.random() < 0.3:
+                D[p] = -1                                   # pin p has no arc
+        ins = []
+        for _ in range(k):
+            n = int(rng.integers(0, 7))
+            ts = np.sort(rng.choice(np.arange(0, 15), size=n, replace=False))
+            vs, prev = [], X
+            for _ in range(n):
+                v = int(rng.choice([x for x in (0, 1, X, Z) if x != prev]))
+                vs.append(v)
+                prev = v
+            ins.append((ts.astype(np.int64), np.array(vs, np.uint8)))
+        vals = lambda F: (0, 1) if F == X else (F,)
+        want, F, cur = [], X, [X] * k
+        for t in range(0, 16):
+            changed = {}
+            for p, (ts, vs) in enumerate(ins):
+                hit = np.nonzero(ts == t)[0]
+                if len(hit):
+                    changed[p] = cls[(cur[p], int(vs[hit[0]]))]
+                    cur[p] = int(vs[hit[0]])
+            if not changed:
+                continue
+            nF = int(lut[sum(v * 4 ** p for p, v in enumerate(cur))])
+            if nF != F:
+                ds = [D[p, e, v] for p, es in changed.items() for e in es for v in vals(nF) if D[p, e, v] > 0]
+                if not ds:
+                    ds = [D[p, e, v] for p in range(k) for e in (0, 1) for v in vals(nF) if D[p, e, v] > 0]
+                want.append((t, t + min(ds), nF))
+            F = nF
+        td, tr, cv = oracle.cell_candidates(lut, D, ins)
+        assert list(zip(td.tolist(), tr.tolist(), cv.tolist())) == want, (trial, lut, D, ins)

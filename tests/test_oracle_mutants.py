@@ -97,7 +97,7 @@ PINS = [
     tn.test_buf_inv_chain_closed_form, tn.test_event_driven_equals_levelized, tn.test_settle_values_equal_static_eval,
     tn.test_invariants_and_eq2_bound, tn.test_same_net_on_both_pins_closed_forms,
     tg.test_edge_classes_golden, tg.test_arc_delay4_cases, tg.test_edge_delay_golden,
-    tg.test_cell_candidates_equal_gate_candidates, tg.test_outputs_are_independent, tg.test_general_invariants,
+    tg.test_cell_candidates_against_time_stepping, tg.test_cell_candidates_equal_gate_candidates, tg.test_outputs_are_independent, tg.test_general_invariants,
     tgate.test_eq1_bruteforce_all_short_sequences,
 ]
 
