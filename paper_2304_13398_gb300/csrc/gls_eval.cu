@@ -46,6 +46,16 @@ namespace gls {
 namespace {
 
 constexpr int PCAP = kPendCap;          // carried (pending) transitions, > GLS_MAX_DELAY_SPREAD
+
+// Window size of the default ('wide') variant and its register cap in the
+// persistent kernel (compile-time tuning knobs).
+#ifndef GLS_WIDE_CH
+#define GLS_WIDE_CH 352
+#endif
+#ifndef GLS_WIDE_MAXNREG
+#define GLS_WIDE_MAXNREG 128
+#endif
+constexpr int kWideCH = GLS_WIDE_CH;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr uint32_t EINF = 0xFFFFFFFFu;  // sentinel event; its time 2^30-1 exceeds every real time
 
@@ -98,6 +108,10 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar) {
 }
 __device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// Orders this thread's generic-proxy accesses of global memory with its
+// async-proxy (bulk copy) accesses: a waveform written with ordinary stores
+// by one warp is read with cp.async.bulk by another in the same launch.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;\n" ::: "memory"); }
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
@@ -1034,13 +1048,13 @@ __device__ __forceinline__ bool eval_variant(const GateRec &gr, const RunDev &r,
         return true;
     }
     if (V == kVariantWindowedWide)
-        return eval_windowed<DEP, 352, MIRROR>(gr, r, reinterpret_cast<WarpSmem<352> *>(smem_raw)[warp], lane, par);
+        return eval_windowed<DEP, kWideCH, MIRROR>(gr, r, reinterpret_cast<WarpSmem<kWideCH> *>(smem_raw)[warp], lane, par);
     return eval_windowed<DEP, 128, MIRROR>(gr, r, reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane, par);
 }
 
 template <int V>
 __device__ __forceinline__ void init_variant(unsigned char *smem_raw, int warp, int lane) {
-    if (V == kVariantWindowedWide) init_window_barriers(reinterpret_cast<WarpSmem<352> *>(smem_raw)[warp], lane);
+    if (V == kVariantWindowedWide) init_window_barriers(reinterpret_cast<WarpSmem<kWideCH> *>(smem_raw)[warp], lane);
     else if (V == kVariantWindowed) init_window_barriers(reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane);
 }
 
@@ -1100,7 +1114,7 @@ __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin,
 // Completion flags are per net: primary inputs start done, a gate's output
 // net is released once its waveform and descriptor are written.
 template <int V, bool MIRROR>
-__global__ void __maxnreg__(V == kVariantWindowed ? 72 : 128) dependency_kernel(const GateRec *__restrict__ gates, int32_t n_gates, int32_t ctr_slot, RunDev r) {
+__global__ void __maxnreg__(V == kVariantWindowed ? 72 : GLS_WIDE_MAXNREG) dependency_kernel(const GateRec *__restrict__ gates, int32_t n_gates, int32_t ctr_slot, RunDev r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t L = 1;
@@ -1124,6 +1138,13 @@ __global__ void __maxnreg__(V == kVariantWindowed ? 72 : 128) dependency_kernel(
             }
         }
         ok = __all_sync(FULL, ok);
+        // Every lane reads the fanin descriptors that lanes 0..k-1 acquired:
+        // the barrier carries their acquires to the whole warp.  The fanin
+        // waveforms were written by generic stores and are fetched by bulk
+        // copies (async proxy) issued by the lane that acquired the pin's
+        // flag, so that lane orders the two proxies first.
+        __syncwarp();
+        if (lane < gr.k) fence_proxy_async_global();
         if (ok) {
             // a window copy that never completed stops the warp (its readers
             // then give up their bounded waits)
@@ -1133,6 +1154,10 @@ __global__ void __maxnreg__(V == kVariantWindowed ? 72 : 128) dependency_kernel(
             r.net_ptr[gr.out_net] = 0;
             r.net_len[gr.out_net] = 0;
         }
+        // publish: this lane's output stores are ordered for the readers' bulk
+        // copies (async proxy) and, through the warp barrier and lane 0's
+        // release, for their acquire of the completion flag
+        fence_proxy_async_global();
         __threadfence();
         __syncwarp();
         if (lane == 0 && g != r.withhold_gate) st_release(r.done + gr.out_net, 1u);
@@ -1143,7 +1168,7 @@ __global__ void __maxnreg__(V == kVariantWindowed ? 72 : 128) dependency_kernel(
 
 size_t gate_smem_bytes(int variant, int warps_per_cta) {
     if (variant == kVariantSegmented) return 0;
-    return (variant == kVariantWindowedWide ? sizeof(WarpSmem<352>) : sizeof(WarpSmem<128>)) * (size_t)warps_per_cta;
+    return (variant == kVariantWindowedWide ? sizeof(WarpSmem<kWideCH>) : sizeof(WarpSmem<128>)) * (size_t)warps_per_cta;
 }
 
 template <int V>
