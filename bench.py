@@ -431,15 +431,17 @@ def run_own(a):
                               "mirror as they go; the step ends when all waveforms and their descriptors are "
                               "in host memory (primary inputs are the caller's stimulus)"}
 
+    # `config` names the workload only (the reference arm prints the same
+    # dict); how this arm ran it goes under `run`
     cfg = describe(a.workload, w)
-    cfg.update({"output_transitions_per_step": e_out, "arena_words": int(arena) if arena else "default",
-                "l2_policy": "inputs larger than L2 (stimulus and intermediate waveforms >> 129 MB)",
-                "parallelism": f"replicas{world}" if world > 1 else "single", "schedule": a.schedule, "kernel": a.kernel,
-                "gate_order": order,
-                "event_format": "packed u32 transitions (t << 2) | v: 30-bit time, 2-bit value 0/1/X/Z"})
+    run_cfg = {"output_transitions_per_step": e_out, "arena_words": int(arena) if arena else "default",
+               "l2_policy": "inputs larger than L2 (stimulus and intermediate waveforms >> 129 MB)",
+               "parallelism": f"replicas{world}" if world > 1 else "single", "schedule": a.schedule,
+               "kernel": a.kernel, "gate_order": order,
+               "event_format": "packed u32 transitions (t << 2) | v: 30-bit time, 2-bit value 0/1/X/Z"}
     peak, peak_kind = measured_peak_gbs()
     achieved = alg_bytes / (k_ms / 1000.0) / 1e9
-    traffic = ncu_traffic(a.workload, cfg)
+    traffic = ncu_traffic(a.workload, dict(cfg, **run_cfg))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind,
             "kernel": (f"dependency_kernel<{a.kernel}> (one launch per run)" if a.schedule == "dependency"
@@ -454,7 +456,7 @@ def run_own(a):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": max(a.warmup, 3), "ms_per_step": ms, "sim_time_ms": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+            "data": "synthetic", "config": cfg, "run": run_cfg, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
             "gpu_launches": launches_per_step * a.steps, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line))

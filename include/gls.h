@@ -128,6 +128,10 @@ const char *gls_last_error(gls_ctx *ctx);
  * gates are reordered by level, one 64-byte record per gate (fanin net ids,
  * delays, the cell's 4-value table); the device copy is immutable.
  * *netlist_id receives a handle.
+ * Paper: the netlist and its cells of Sec. 2.1 (objective statement), each
+ * cell's 4-value function of Sec. 2.2 / Table 1 built per Sec. 3.3 (module
+ * function), and the pin-to-pin delays of Sec. 2.3 kept as the delay matrix
+ * of Sec. 3.2 (rise/fall per arc for both input edges in this classic form).
  */
 int gls_load_netlist(gls_ctx *ctx, int32_t n_pi, int32_t n_gates, const uint8_t *type,
                      const int32_t *fanin_off, const int32_t *fanin_net, const int32_t *d_rise,
@@ -139,6 +143,10 @@ int gls_load_netlist(gls_ctx *ctx, int32_t n_pi, int32_t n_gates, const uint8_t 
  * transition into one 32-bit word.  Synchronous.  GLS_ESTIM on a rule
  * violation.  *stim_id receives a handle usable with any netlist of the same
  * n_pi.
+ * Paper: the given waveforms of Sec. 2.1, moved to the device in the single
+ * transfer before the one-pass evaluation (Sec. 3, Sec. 1.4 algorithmic flow).
+ * The stimulus is a handle of its own (n_pi, not a netlist id): one stimulus
+ * serves every netlist with that many primary inputs.
  */
 int gls_load_stimulus(gls_ctx *ctx, int32_t n_pi, const int64_t *off, const int32_t *t,
                       const uint8_t *v, int32_t *stim_id);
@@ -153,6 +161,15 @@ int gls_update_stimulus(gls_ctx *ctx, int32_t stim_id, const int64_t *off, const
                         const uint8_t *v);
 
 /*
+ * Paper: the one-pass evaluation of Sec. 4 -- Algorithm 1 (every cell is
+ * processed once its input waveforms are known; here as one persistent
+ * launch in a topological order, or one launch per level) and Algorithm 2 per
+ * gate (merge of the fanin waveforms, 4-value function, minimum delay over the
+ * changed pins of Sec. 2.3, "glitch eaten" cancellation of Eq. 1), each output
+ * reserving its Eq. 2 bound in the device store (Sec. 3.1).  arena_events is
+ * the one parameter beyond the paper: the size of that store, which the
+ * paper's CSRP allocates up front as well (Eq. 4).
+ *
  * Simulate a netlist under a stimulus: allocate the run's waveform store
  * (net descriptors plus an event arena of arena_events 32-bit words; 0 means
  * 256 words per stimulus transition plus 2^20, capped at half of the unused
@@ -232,6 +249,8 @@ int gls_run_info(gls_ctx *ctx, int32_t run_id, int64_t *arena_demand, int64_t *a
 int gls_plan_order(gls_ctx *ctx, int32_t netlist_id, int32_t run_id, int32_t item);
 
 /*
+ * Paper: a waveform of the device store (Sec. 3.1, CSR rows), copied out.
+ *
  * Copy one net's waveform to the host (item 0 of a batch): times into
  * t[cap], values into v[cap].  *n_out always receives the length; GLS_EOVERFLOW if cap < length
  * (nothing copied).  Synchronises with the run.
@@ -240,6 +259,9 @@ int gls_read_waveform(gls_ctx *ctx, int32_t run_id, int32_t net, int32_t *t, uin
                       int64_t cap, int64_t *n_out);
 
 /*
+ * Paper: the whole store as one CSR (Sec. 3.1) in the single transfer back to
+ * the host after the one-pass evaluation (Sec. 3).
+ *
  * Copy every net's waveform to the host as one CSR: off[n_nets+1] (int64,
  * caller-allocated) and packed[cap] transitions, each (time << 2) | value,
  * nets in id order.  The device gathers the store into net order first so the

@@ -5,8 +5,9 @@ of 128 or 352 transitions per pin of 3-input cells, longer for fewer
 inputs, i.e. the event chunk size; or one lane per time segment with a
 given segment size) and the CTA shape.  Each candidate builds
 the caller's run, runs it once to warm up, then times `reruns` evaluations
-with the library's own device timer; the fastest configuration is left
-applied to the context and returned.  Results are identical for every
+with the library's own device timer and scores the candidate by the median
+(an odd count, so the median is one measured run); the fastest configuration
+is left applied to the context and returned.  Results are identical for every
 candidate (all variants are parity-tested), so tuning only affects speed.
 """
 from __future__ import annotations
@@ -38,9 +39,11 @@ def apply(ctx, cand: dict):
         ctx.set_option(_g.GLS_OPT_SEGMENT, cand["segment"])
 
 
-def autotune(ctx, build_run, candidates=None, reruns: int = 2) -> TuneResult:
+def autotune(ctx, build_run, candidates=None, reruns: int = 3) -> TuneResult:
     """build_run() -> run id of a freshly created run of the workload (it is
     released here).  Returns the fastest candidate, applied to ctx."""
+    if reruns < 1 or reruns % 2 == 0:
+        raise ValueError("reruns must be a positive odd count (the score is their median)")
     cands = candidates or DEFAULT_CANDIDATES
     times = []
     for cand in cands:
