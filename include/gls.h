@@ -223,10 +223,15 @@ int gls_run_query(gls_ctx *ctx, int32_t run_id);
  */
 int gls_run_stats(gls_ctx *ctx, int32_t run_id, int64_t *total_events, double *kernel_ms);
 
-/* Wait for a run and report its event arena: *arena_demand = words the gates
-   reserved (Eq. 2 bounds, padded to 128-byte lines), *arena_capacity = the
-   run's arena size; either pointer may be NULL.  The demand sizes later runs
-   of similar inputs (the serving admission model). */
+/* Wait for a run and report its event arena: *arena_demand = words claimed
+   from it, *arena_capacity = the run's arena size; either pointer may be
+   NULL.  The warps of a run claim the arena in blocks; each gate reserves its
+   Eq. 2 bound inside its warp's block while it runs and keeps only its
+   waveform (both padded to 128-byte lines), so the demand is the output
+   (padded) plus the unused ends of the blocks -- at most about a sixteenth of
+   the arena, and it varies by that much from run to run with the order in
+   which the warps take the gates.  The demand sizes later runs of similar
+   inputs (the serving admission model). */
 int gls_run_info(gls_ctx *ctx, int32_t run_id, int64_t *arena_demand, int64_t *arena_capacity);
 
 /*
@@ -404,11 +409,17 @@ typedef enum gls_option {
                                    of their event arena as the kernels write it, so the results
                                    reach host memory while the simulation runs (gls_read_host);
                                    0 (default): results stay on the device until read */
-    GLS_OPT_POOL_BYTES = 7      /* > 0: allocate one device region of this size now and carve
+    GLS_OPT_POOL_BYTES = 7,     /* > 0: allocate one device region of this size now and carve
                                    every later netlist, stimulus and run buffer from it (first
                                    fit, no cudaMalloc/cudaFree per run, so creating and freeing
                                    runs does not synchronise the device); 0: free the pool.
                                    Only when no pool block is in use. */
+    GLS_OPT_HOST_POOL_BYTES = 9 /* > 0: allocate one pinned, device-mapped host region of this
+                                   size now and carve the host mirrors of later runs
+                                   (GLS_OPT_HOST_MIRROR) from it, first fit, instead of pinning
+                                   new host memory per run; GLS_ENOMEM at run creation when no
+                                   block is large enough.  0: free it.  Only when no mirror is
+                                   in use. */
 } gls_option;
 
 /* Gate kernel variants; all compute the same waveforms.

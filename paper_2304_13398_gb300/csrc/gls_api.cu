@@ -352,6 +352,14 @@ struct RunObj {
 
 }  // namespace
 
+// One region carved first-fit into 256-byte aligned blocks.
+struct Pool {
+    char *base = nullptr;
+    uint64_t bytes = 0;
+    std::map<uint64_t, uint64_t> free;            // offset -> size of free ranges
+    std::unordered_map<void *, uint64_t> allocs;  // block -> size
+};
+
 struct gls_ctx {
     int device = 0;
     uint64_t budget = 0, used = 0;
@@ -369,10 +377,11 @@ struct gls_ctx {
     std::unordered_map<int32_t, std::unique_ptr<RunObj>> runs;
     std::unordered_map<void *, size_t> allocs;       // cudaMalloc'd blocks
     // optional device pool: one region carved first-fit into 256-byte aligned blocks
-    char *pool = nullptr;
-    uint64_t pool_bytes = 0;
-    std::map<uint64_t, uint64_t> pool_free;           // offset -> size of free ranges
-    std::unordered_map<void *, uint64_t> pool_allocs; // block -> size
+    Pool pool;
+    // optional pinned host pool for the host mirrors of runs (GLS_OPT_HOST_POOL_BYTES),
+    // mapped into the device's address space at hpool_dev
+    Pool hpool;
+    char *hpool_dev = nullptr;
     uint32_t *d_status = nullptr;       // scratch for stimulus packing (3 words)
     std::vector<UserCell> cells;        // gls_define_cell, type GLS_USER_CELL_BASE + index
 };
@@ -384,61 +393,67 @@ namespace {
 // Long-lived objects (netlists, stimuli, planned orders) are carved from the
 // top of the pool and runs from the bottom, so releasing a run leaves one
 // large free range instead of gaps between persistent blocks.
-void *pool_take(gls_ctx *c, uint64_t bytes, bool persistent) {
+void *pool_take(Pool &pl, uint64_t bytes, bool persistent) {
     bytes = (bytes + 255) & ~255ull;
     if (persistent) {
-        for (auto it = c->pool_free.rbegin(); it != c->pool_free.rend(); ++it) {
+        for (auto it = pl.free.rbegin(); it != pl.free.rend(); ++it) {
             if (it->second < bytes) continue;
             const uint64_t off = it->first, size = it->second;
             if (size > bytes) it->second = size - bytes;
-            else c->pool_free.erase(std::next(it).base());
-            void *p = c->pool + off + size - bytes;
-            c->pool_allocs[p] = bytes;
+            else pl.free.erase(std::next(it).base());
+            void *p = pl.base + off + size - bytes;
+            pl.allocs[p] = bytes;
             return p;
         }
         return nullptr;
     }
-    for (auto it = c->pool_free.begin(); it != c->pool_free.end(); ++it) {
+    for (auto it = pl.free.begin(); it != pl.free.end(); ++it) {
         if (it->second < bytes) continue;
         const uint64_t off = it->first, size = it->second;
-        c->pool_free.erase(it);
-        if (size > bytes) c->pool_free[off + bytes] = size - bytes;
-        void *p = c->pool + off;
-        c->pool_allocs[p] = bytes;
+        pl.free.erase(it);
+        if (size > bytes) pl.free[off + bytes] = size - bytes;
+        void *p = pl.base + off;
+        pl.allocs[p] = bytes;
         return p;
     }
     return nullptr;
 }
 
-bool pool_give(gls_ctx *c, void *p) {
-    auto a = c->pool_allocs.find(p);
-    if (a == c->pool_allocs.end()) return false;
-    uint64_t off = (uint64_t)((char *)p - c->pool), size = a->second;
-    c->pool_allocs.erase(a);
-    auto next = c->pool_free.lower_bound(off);
-    if (next != c->pool_free.end() && next->first == off + size) {   // merge with the following range
+bool pool_give(Pool &pl, void *p) {
+    auto a = pl.allocs.find(p);
+    if (a == pl.allocs.end()) return false;
+    uint64_t off = (uint64_t)((char *)p - pl.base), size = a->second;
+    pl.allocs.erase(a);
+    auto next = pl.free.lower_bound(off);
+    if (next != pl.free.end() && next->first == off + size) {   // merge with the following range
         size += next->second;
-        next = c->pool_free.erase(next);
+        next = pl.free.erase(next);
     }
-    if (next != c->pool_free.begin()) {                               // and with the preceding one
+    if (next != pl.free.begin()) {                               // and with the preceding one
         auto prev = std::prev(next);
         if (prev->first + prev->second == off) {
             prev->second += size;
             return true;
         }
     }
-    c->pool_free[off] = size;
+    pl.free[off] = size;
     return true;
+}
+
+uint64_t pool_largest_free(const Pool &pl) {
+    uint64_t m = 0;
+    for (auto &kv : pl.free) m = std::max(m, kv.second);
+    return m;
 }
 
 int dalloc(gls_ctx *c, void **p, size_t bytes, bool persistent = false) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    if (c->pool) {
-        *p = pool_take(c, bytes, persistent);
+    if (c->pool.base) {
+        *p = pool_take(c->pool, bytes, persistent);
         if (!*p)
             return fail(GLS_ENOMEM, "device pool of %llu bytes has no free block of %llu bytes",
-                        (unsigned long long)c->pool_bytes, (unsigned long long)bytes);
+                        (unsigned long long)c->pool.bytes, (unsigned long long)bytes);
         return GLS_OK;
     }
     if (c->used + bytes > c->budget)
@@ -465,7 +480,7 @@ int dalloc_n(gls_ctx *c, T **p, size_t n, bool persistent = false) {
 
 void dfree(gls_ctx *c, void *p) {
     if (!p) return;
-    if (pool_give(c, p)) return;
+    if (pool_give(c->pool, p)) return;
     auto it = c->allocs.find(p);
     if (it != c->allocs.end()) {
         c->used -= it->second;
@@ -506,7 +521,7 @@ void free_run(gls_ctx *c, RunObj *r) {
     dfree(c, r->d_gather);
     dfree(c, r->d_slice_packed);
     dfree(c, r->d_glen);
-    if (r->h_arena) cudaFreeHost(r->h_arena);
+    if (r->h_arena && !pool_give(c->hpool, r->h_arena)) cudaFreeHost(r->h_arena);
     for (int k = 0; k < 2; k++) {
         dfree(c, r->d_st[k]);
         dfree(c, r->d_pend[k]);
@@ -709,10 +724,7 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
         // default: 256 words per stimulus transition plus 1 Mi, at most half
         // of what is left of the budget (GLS_EOVERFLOW reports the demand)
         uint64_t left = c->budget > c->used ? c->budget - c->used : 0;
-        if (c->pool) {
-            left = 0;
-            for (auto &kv : c->pool_free) left = std::max(left, kv.second);
-        }
+        if (c->pool.base) left = pool_largest_free(c->pool);
         uint64_t meta = (uint64_t)r->n_nets * 16 + (uint64_t)r->depth * 4 + 4096;
         uint64_t cap = left > meta ? (left - meta) / 2 / 4 : 0;
         uint64_t want = 256ull * (uint64_t)stim_events + (1ull << 20);
@@ -725,6 +737,14 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
     }
     const int64_t N = r->n_nets;
     r->dev.arena_cap = (uint64_t)arena_events;
+    {   // warps claim the arena in blocks of about a sixteenth of their share per
+        // launch (at most 32 Ki words), so the unused block tails stay a few
+        // percent of the arena; below one line every gate claims its own slot
+        const uint64_t warps = (uint64_t)std::max(1, c->cfg.ctas * c->cfg.warps_per_cta);
+        const uint64_t launches = r->schedule == GLS_SCHEDULE_DEPENDENCY ? 1 : (uint64_t)std::max(1, r->depth);
+        const uint64_t blk = std::min<uint64_t>((uint64_t)arena_events / (16 * warps * launches), 32768);
+        r->dev.arena_blk = (uint32_t)(blk & ~(uint64_t)(kSlotAlign - 1));
+    }
     r->dev.n_pi = 0;
     r->dev.n_gates = r->n_gates;
     r->dev.wait_limit_ns = c->wait_limit_ns;
@@ -747,14 +767,26 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
             free_run(c, r.get());
             return fail(GLS_EINVAL, "host-mirrored results need the windowed kernels");
         }
+        const size_t mbytes = sizeof(uint32_t) * ((size_t)arena_events + 2 * kSlotAlign);
         void *h = nullptr, *d = nullptr;
-        cudaError_t e = cudaHostAlloc(&h, sizeof(uint32_t) * ((size_t)arena_events + 2 * kSlotAlign), cudaHostAllocMapped);
-        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&d, h, 0);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            if (h) cudaFreeHost(h);
-            free_run(c, r.get());
-            return fail(GLS_ENOMEM, "pinned host mirror of %lld words: %s", (long long)arena_events, cudaGetErrorString(e));
+        if (c->hpool.base) {   // carved from the pinned host pool: no allocation call per run
+            h = pool_take(c->hpool, mbytes, false);
+            if (!h) {
+                free_run(c, r.get());
+                return fail(GLS_ENOMEM, "host pool of %llu bytes has no free block for a mirror of %zu bytes",
+                            (unsigned long long)c->hpool.bytes, mbytes);
+            }
+            d = c->hpool_dev + ((char *)h - c->hpool.base);
+        } else {
+            cudaError_t e = cudaHostAlloc(&h, mbytes, cudaHostAllocMapped);
+            if (e == cudaSuccess) e = cudaHostGetDevicePointer(&d, h, 0);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                if (h) cudaFreeHost(h);
+                free_run(c, r.get());
+                return fail(GLS_ENOMEM, "pinned host mirror of %lld words: %s", (long long)arena_events,
+                            cudaGetErrorString(e));
+            }
         }
         r->h_arena = static_cast<uint32_t *>(h);
         r->dev.harena = static_cast<uint32_t *>(d);
@@ -929,7 +961,8 @@ void gls_destroy(gls_ctx *c) {
     for (auto &kv : c->stims) free_stim(c, kv.second.get());
     for (auto &kv : c->netlists) free_netlist(c, kv.second.get());
     dfree(c, c->d_status);
-    if (c->pool) cudaFree(c->pool);
+    if (c->pool.base) cudaFree(c->pool.base);
+    if (c->hpool.base) cudaFreeHost(c->hpool.base);
     cudaStreamDestroy(c->stream);
     cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -1535,13 +1568,11 @@ int gls_set_option(gls_ctx *c, int option, int64_t value) {
         return GLS_OK;
     case GLS_OPT_POOL_BYTES: {
         if (value < 0) return fail(GLS_EINVAL, "pool size must be >= 0");
-        if (!c->pool_allocs.empty()) return fail(GLS_EINVAL, "the pool still holds %zu blocks", c->pool_allocs.size());
-        if (c->pool) {
-            CK(cudaFree(c->pool));
-            c->used -= c->pool_bytes;
-            c->pool = nullptr;
-            c->pool_bytes = 0;
-            c->pool_free.clear();
+        if (!c->pool.allocs.empty()) return fail(GLS_EINVAL, "the pool still holds %zu blocks", c->pool.allocs.size());
+        if (c->pool.base) {
+            CK(cudaFree(c->pool.base));
+            c->used -= c->pool.bytes;
+            c->pool = Pool{};
         }
         if (value == 0) return GLS_OK;
         const uint64_t bytes = ((uint64_t)value + 255) & ~255ull;
@@ -1553,10 +1584,36 @@ int gls_set_option(gls_ctx *c, int option, int64_t value) {
             cudaGetLastError();
             return fail(GLS_ENOMEM, "cudaMalloc(pool %llu): %s", (unsigned long long)bytes, cudaGetErrorString(e));
         }
-        c->pool = static_cast<char *>(p);
-        c->pool_bytes = bytes;
+        c->pool.base = static_cast<char *>(p);
+        c->pool.bytes = bytes;
         c->used += bytes;
-        c->pool_free[0] = bytes;
+        c->pool.free[0] = bytes;
+        return GLS_OK;
+    }
+    case GLS_OPT_HOST_POOL_BYTES: {
+        if (value < 0) return fail(GLS_EINVAL, "host pool size must be >= 0");
+        if (!c->hpool.allocs.empty())
+            return fail(GLS_EINVAL, "the host pool still holds %zu mirrors", c->hpool.allocs.size());
+        if (c->hpool.base) {
+            CK(cudaFreeHost(c->hpool.base));
+            c->hpool = Pool{};
+            c->hpool_dev = nullptr;
+        }
+        if (value == 0) return GLS_OK;
+        const uint64_t bytes = ((uint64_t)value + 255) & ~255ull;
+        void *h = nullptr, *d = nullptr;
+        cudaError_t e = cudaHostAlloc(&h, bytes, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&d, h, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (h) cudaFreeHost(h);
+            return fail(GLS_ENOMEM, "pinned host pool of %llu bytes: %s", (unsigned long long)bytes,
+                        cudaGetErrorString(e));
+        }
+        c->hpool.base = static_cast<char *>(h);
+        c->hpool.bytes = bytes;
+        c->hpool.free[0] = bytes;
+        c->hpool_dev = static_cast<char *>(d);
         return GLS_OK;
     }
     case GLS_OPT_TEST_WITHHOLD_GATE:

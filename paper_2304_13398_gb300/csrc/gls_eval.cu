@@ -92,6 +92,19 @@ struct __align__(16) WarpSmem {
     __device__ __forceinline__ uint32_t *window(int b, int p) { return &win[0][0][0] + p * (chunk<K>() + 8); }
 };
 
+// A warp's current block of the event arena, [cur, end).  The gates a warp
+// evaluates take their output slots from it one after another: a slot is the
+// gate's Eq. 2 bound (rounded up to whole 128-byte lines) while the gate
+// runs and shrinks to its actual length (rounded up likewise) when the gate
+// is done, so the arena holds about the real output instead of the bounds.
+// A gate whose bound does not fit the rest of the block claims a new block of
+// max(bound, r.arena_blk) words with one atomicAdd on the arena top (the rest
+// of the old block stays unused); r.arena_blk = 0 gives every gate a slot of
+// its own, exactly its bound.
+struct WarpArena {
+    unsigned long long cur, end;
+};
+
 // Running state of one gate's output between chunks.
 struct CommitState {
     uint32_t outCount;   // transitions written
@@ -333,7 +346,8 @@ __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0,
 // Returns false only when a window copy did not complete within its poll
 // bound (the warp then stops: its buffers may still be written).
 template <int K, bool DEP, int CH, bool EDGE, bool MIRROR>
-__device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane, uint32_t &par) {
+__device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane, uint32_t &par,
+                          WarpArena &wa) {
     GateCtx g;
     uint64_t bound = 0;
 #pragma unroll
@@ -386,8 +400,11 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
     // Claim the output slot and start the first window copies before the
     // per-gate tables are built, so that the atomic's and the copies'
     // latencies overlap that work.
+    const uint64_t need = (bound + kSlotAlign - 1) & ~(uint64_t)(kSlotAlign - 1);
+    const bool claim = wa.cur + need > wa.end;   // the same on every lane
+    const uint64_t blk = need > r.arena_blk ? need : (uint64_t)r.arena_blk;
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(r.arena_top, (unsigned long long)((bound + kSlotAlign - 1) & ~(uint64_t)(kSlotAlign - 1)));
+    if (claim && lane == 0) base = atomicAdd(r.arena_top, (unsigned long long)blk);
     uint32_t cur[3] = {0, 0, 0};
     bool failed = false;
     const int b = 0;   // the one window buffer
@@ -466,8 +483,14 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         }
         __syncwarp();
     }
-    base = __shfl_sync(FULL, base, 0);
+    if (claim) {
+        base = __shfl_sync(FULL, base, 0);
+        wa.end = base + blk;
+    } else {
+        base = wa.cur;
+    }
     if (base + bound > r.arena_cap) {
+        wa.cur = wa.end = 0;   // past the arena: the next gate claims again (and counts its demand)
         if (lane == 0) {
             atomicOr(r.status, kStArenaOverflow);
             r.net_ptr[out_net] = 0;
@@ -729,23 +752,25 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         r.net_ptr[out_net] = reinterpret_cast<uint64_t>(out);
         r.net_len[out_net] = failed ? 0u : cs.outCount;
     }
+    // the slot shrinks to the waveform, whole lines (no two nets share one)
+    wa.cur = base + (failed ? need : (((uint64_t)cs.outCount + kSlotAlign - 1) & ~(uint64_t)(kSlotAlign - 1)));
     return true;
 }
 
 template <bool DEP, int CH, bool MIRROR>
 __device__ __forceinline__ bool eval_windowed(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane,
-                                              uint32_t &par) {
+                                              uint32_t &par, WarpArena &wa) {
     if (gr.flags & kGateEdge) {
         switch (gr.k) {
-        case 1: return eval_gate<1, DEP, CH, true, MIRROR>(gr, r, sm, lane, par);
-        case 2: return eval_gate<2, DEP, CH, true, MIRROR>(gr, r, sm, lane, par);
-        default: return eval_gate<3, DEP, CH, true, MIRROR>(gr, r, sm, lane, par);
+        case 1: return eval_gate<1, DEP, CH, true, MIRROR>(gr, r, sm, lane, par, wa);
+        case 2: return eval_gate<2, DEP, CH, true, MIRROR>(gr, r, sm, lane, par, wa);
+        default: return eval_gate<3, DEP, CH, true, MIRROR>(gr, r, sm, lane, par, wa);
         }
     }
     switch (gr.k) {
-    case 1: return eval_gate<1, DEP, CH, false, MIRROR>(gr, r, sm, lane, par);
-    case 2: return eval_gate<2, DEP, CH, false, MIRROR>(gr, r, sm, lane, par);
-    default: return eval_gate<3, DEP, CH, false, MIRROR>(gr, r, sm, lane, par);
+    case 1: return eval_gate<1, DEP, CH, false, MIRROR>(gr, r, sm, lane, par, wa);
+    case 2: return eval_gate<2, DEP, CH, false, MIRROR>(gr, r, sm, lane, par, wa);
+    default: return eval_gate<3, DEP, CH, false, MIRROR>(gr, r, sm, lane, par, wa);
     }
 }
 
@@ -840,7 +865,7 @@ __device__ __forceinline__ uint32_t lower_bound_t(const uint32_t *a, uint32_t n,
 }
 
 template <int K, bool DEP>
-__device__ void eval_gate_seg(const GateRec &gr, const RunDev &r, int lane) {
+__device__ void eval_gate_seg(const GateRec &gr, const RunDev &r, int lane, WarpArena &wa) {
     const uint32_t *src[3];
     uint32_t len[3], rise[3], fall[3];
     uint64_t bound = 0;
@@ -865,10 +890,18 @@ __device__ void eval_gate_seg(const GateRec &gr, const RunDev &r, int lane) {
         if (lane == 0) { r.net_ptr[out_net] = 0; r.net_len[out_net] = 0; }
         return;
     }
+    const uint64_t need = (bound + kSlotAlign - 1) & ~(uint64_t)(kSlotAlign - 1);
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(r.arena_top, (unsigned long long)((bound + kSlotAlign - 1) & ~(uint64_t)(kSlotAlign - 1)));
-    base = __shfl_sync(FULL, base, 0);
+    if (wa.cur + need > wa.end) {   // claim a new block (the same decision on every lane)
+        const uint64_t blk = need > r.arena_blk ? need : (uint64_t)r.arena_blk;
+        if (lane == 0) base = atomicAdd(r.arena_top, (unsigned long long)blk);
+        base = __shfl_sync(FULL, base, 0);
+        wa.end = base + blk;
+    } else {
+        base = wa.cur;
+    }
     if (base + bound > r.arena_cap) {
+        wa.cur = wa.end = 0;
         if (lane == 0) {
             atomicOr(r.status, kStArenaOverflow);
             r.net_ptr[out_net] = 0;
@@ -1026,14 +1059,15 @@ __device__ void eval_gate_seg(const GateRec &gr, const RunDev &r, int lane) {
         r.net_ptr[out_net] = reinterpret_cast<uint64_t>(slot);
         r.net_len[out_net] = total;
     }
+    wa.cur = base + (((uint64_t)total + kSlotAlign - 1) & ~(uint64_t)(kSlotAlign - 1));
 }
 
 template <bool DEP>
-__device__ __forceinline__ void eval_segmented(const GateRec &gr, const RunDev &r, int lane) {
+__device__ __forceinline__ void eval_segmented(const GateRec &gr, const RunDev &r, int lane, WarpArena &wa) {
     switch (gr.k) {
-    case 1: eval_gate_seg<1, DEP>(gr, r, lane); break;
-    case 2: eval_gate_seg<2, DEP>(gr, r, lane); break;
-    default: eval_gate_seg<3, DEP>(gr, r, lane); break;
+    case 1: eval_gate_seg<1, DEP>(gr, r, lane, wa); break;
+    case 2: eval_gate_seg<2, DEP>(gr, r, lane, wa); break;
+    default: eval_gate_seg<3, DEP>(gr, r, lane, wa); break;
     }
 }
 
@@ -1042,14 +1076,15 @@ __device__ __forceinline__ void eval_segmented(const GateRec &gr, const RunDev &
 // V = kVariantSegmented or kVariantWindowed
 template <int V, bool DEP, bool MIRROR>
 __device__ __forceinline__ bool eval_variant(const GateRec &gr, const RunDev &r, unsigned char *smem_raw,
-                                             int warp, int lane, uint32_t &par) {
+                                             int warp, int lane, uint32_t &par, WarpArena &wa) {
     if (V == kVariantSegmented) {
-        seg::eval_segmented<DEP>(gr, r, lane);
+        seg::eval_segmented<DEP>(gr, r, lane, wa);
         return true;
     }
     if (V == kVariantWindowedWide)
-        return eval_windowed<DEP, kWideCH, MIRROR>(gr, r, reinterpret_cast<WarpSmem<kWideCH> *>(smem_raw)[warp], lane, par);
-    return eval_windowed<DEP, 128, MIRROR>(gr, r, reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane, par);
+        return eval_windowed<DEP, kWideCH, MIRROR>(gr, r, reinterpret_cast<WarpSmem<kWideCH> *>(smem_raw)[warp], lane,
+                                                   par, wa);
+    return eval_windowed<DEP, 128, MIRROR>(gr, r, reinterpret_cast<WarpSmem<128> *>(smem_raw)[warp], lane, par, wa);
 }
 
 template <int V>
@@ -1094,13 +1129,14 @@ __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin,
     int32_t L = level + 1;
     init_variant<V>(smem_raw, warp, lane);
     uint32_t par = 0;   // phase parities of the warp's window barriers
+    WarpArena wa{0, 0};  // no block yet
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(r.level_ctr + level, 1);
         g = __shfl_sync(FULL, g, 0);
         if (g >= g_count) break;
         const GateRec gr = fetch_gate(gates, r, (int64_t)g_begin + g, L);
-        if (!eval_variant<V, false, MIRROR>(gr, r, smem_raw, warp, lane, par)) break;
+        if (!eval_variant<V, false, MIRROR>(gr, r, smem_raw, warp, lane, par, wa)) break;
         __syncwarp();
     }
 }
@@ -1120,6 +1156,7 @@ __global__ void __maxnreg__(V == kVariantWindowed ? 72 : GLS_WIDE_MAXNREG) depen
     int32_t L = 1;
     init_variant<V>(smem_raw, warp, lane);
     uint32_t par = 0;   // phase parities of the warp's window barriers
+    WarpArena wa{0, 0};  // no block yet
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(r.level_ctr + ctr_slot, 1);
@@ -1148,7 +1185,7 @@ __global__ void __maxnreg__(V == kVariantWindowed ? 72 : GLS_WIDE_MAXNREG) depen
         if (ok) {
             // a window copy that never completed stops the warp (its readers
             // then give up their bounded waits)
-            if (!eval_variant<V, true, MIRROR>(gr, r, smem_raw, warp, lane, par)) break;
+            if (!eval_variant<V, true, MIRROR>(gr, r, smem_raw, warp, lane, par, wa)) break;
         } else if (lane == 0) {
             atomicOr(r.status, kStTimeout);
             r.net_ptr[gr.out_net] = 0;

@@ -57,6 +57,8 @@ struct RunDev {
     uint32_t *arena;          // [arena_cap] gate output transitions
     uint64_t arena_cap;       // capacity in transitions
     unsigned long long *arena_top;  // bump pointer (transitions), counts demand past cap
+    uint32_t arena_blk;       // words a warp claims from the arena at a time, a multiple of kSlotAlign
+                              // (0: every gate claims exactly its own slot)
     uint32_t *status;         // kSt* bits
     int32_t *level_ctr;       // [depth + 1] work counters, zeroed per run (last: dependency mode)
     uint32_t *done;           // [N] per-net completion flags (dependency mode): PIs 1, gates 0 per run

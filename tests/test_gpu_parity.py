@@ -82,9 +82,12 @@ def _exact_lengths(n, lens, seed):
 
 
 def test_window_boundary_lengths(ctx):
-    # every 2- and 3-input cell on PI waveforms whose lengths straddle the
-    # window size (127/128/129, 255/256/257) and the 32-lane split
-    lens_sets = [[127, 128, 129], [1, 128, 256], [255, 256, 257], [31, 32, 33], [0, 129, 64], [0, 0, 5]]
+    # every cell on PI waveforms whose lengths straddle the per-pin window
+    # sizes of both windowed variants (3-, 2- and 1-input cells: 128 / 192 /
+    # 384 and 352 / 528 / 1056 transitions), other sizes, and the 32-lane split
+    lens_sets = [[127, 128, 129], [1, 128, 256], [255, 256, 257], [31, 32, 33], [0, 129, 64], [0, 0, 5],
+                 [63, 64, 65], [159, 160, 161], [191, 192, 193], [383, 384, 385], [527, 528, 529],
+                 [1055, 1056, 1057], [161, 529, 1057], [351, 352, 353], [353, 705, 1057]]
     for cell in range(11):
         k = oracle.ARITY[cell]
         for li, lens in enumerate(lens_sets):
