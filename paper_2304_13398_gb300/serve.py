@@ -12,10 +12,17 @@ resident stimulus.  The dispatcher:
     are shared, not copied) -- requests that arrive while others run are
     admitted into new launches on other streams, so their work overlaps;
   - retires finished launches with a non-blocking query, records each
-    request's latency (arrival -> results resident on the device) and
-    re-admits a launch whose arena was too small with the measured demand.
-Device buffers come from the context's pool, so admitting and retiring never
-synchronises the device.  policy="sjf" admits the waiting request with the
+    request's latency and re-admits a launch whose arena was too small with
+    the measured demand.
+Latency is request arrival -> its waveforms in host memory (results="host",
+the default): the launches are created with the context's host mirror, so
+the kernels store every output transition into pinned host memory while they
+run, and a request is done once its run has finished and its per-gate
+(offset, length) descriptors have been copied to the host (gls_read_host);
+results="device" stops the clock when the waveforms are resident on the
+device.  Device buffers come from the context's pool and host mirrors from
+its pinned host pool (GLS_OPT_POOL_BYTES, GLS_OPT_HOST_POOL_BYTES), so
+admitting and retiring never synchronises the device.  policy="sjf" admits the waiting request with the
 least estimated work first (shortest job first: small windows do not queue
 behind large ones); "fifo" admits in arrival order.  With max_wait_s, a
 request that has waited longer than that is admitted before any shorter one
@@ -47,6 +54,7 @@ class Request:
     out_transitions: int = 0
     attempts: int = 0
     result: tuple | None = None   # (off, packed) when the server keeps results
+    host_gates: object = None     # with results="host" and kept results: the gates' words from the mirror
 
 
 @dataclass
@@ -58,6 +66,7 @@ class Resident:
     pi_events: int
     window: int
     words_per_event: float = 0.0
+    out_per_event: float = 0.0   # gate-output transitions per stimulus transition (calibration run)
 
 
 @dataclass
@@ -78,9 +87,18 @@ class ServeStats:
 class Server:
     def __init__(self, ctx: Context, budget_bytes: int, max_batch: int = 16, streams: int = 4,
                  batching: bool = True, safety: float = 1.3, keep_results: bool = False, policy: str = "sjf",
-                 stream_factory=None, max_wait_s: float | None = None):
+                 stream_factory=None, max_wait_s: float | None = None, results: str = "host",
+                 host_budget_bytes: int | None = None):
         """stream_factory() makes one launch stream (default: a new CUDA
-        stream); the dispatcher only hands the streams to the context."""
+        stream); the dispatcher only hands the streams to the context.
+        results: "host" (latency ends with the waveforms in host memory) or
+        "device" (resident on the device).  host_budget_bytes: with results
+        "host", the pinned host memory the launches in flight may hold for
+        their mirrors (the context's host pool; None: not checked)."""
+        if results not in ("host", "device"):
+            raise ValueError(results)
+        self.results = results
+        self.host_budget = host_budget_bytes
         if stream_factory is None:
             import torch
             stream_factory = torch.cuda.Stream
@@ -103,12 +121,15 @@ class Server:
         self.res[key] = Resident(key, nid, sid, int(netlist.n_pi + netlist.n_gates), int(stimulus.n_events),
                                  int(window))
 
-    def calibrate(self, frac: float = 0.2, plan: bool = True):
+    def calibrate(self, frac: float = 1.0, plan: bool = True):
         """Event-arena words per stimulus transition of each resident netlist,
         from one run over the first `frac` of its window (the footprint model
-        of admission; transitions are spread evenly over the window).  With
-        plan, the same run also plans the netlist's critical-path-first gate
-        order for the dependency schedule (gls_plan_order)."""
+        of admission; transitions are spread evenly over the window).  The
+        whole window is the default: nets start at X, so the first part of a
+        window carries fewer output transitions per input transition than
+        the rest, and a model taken there would fall short for long windows.
+        With plan, the same run also plans the netlist's critical-path-first
+        gate order for the dependency schedule (gls_plan_order)."""
         for r in self.res.values():
             t_limit = max(1, int(r.window * frac))
             arena = 0
@@ -116,6 +137,7 @@ class Server:
                 rid = self.ctx.simulate_batch([r.nid], [r.sid], t_limits=[t_limit], arena_events=arena)
                 rc, demand, _ = self.ctx.run_stats_raw(rid)
                 if rc == 0:
+                    r.out_per_event = demand / max(1.0, r.pi_events * frac)
                     demand = self.ctx.run_info(rid)[0]
                     if plan:
                         self.ctx.plan_order(r.nid, rid)
@@ -132,11 +154,36 @@ class Server:
         frac = min(1.0, max(t_limit, 1) / r.window)
         return int(r.words_per_event * r.pi_events * frac * self.safety) + 4096
 
+    def expected_transitions(self, key: str, t_limit: int) -> float:
+        """Gate-output transitions a request is expected to produce (the
+        calibration run's output per stimulus transition x the window's
+        stimulus transitions)."""
+        r = self.res[key]
+        return r.out_per_event * r.pi_events * min(1.0, max(t_limit, 1) / r.window)
+
     def _footprint(self, words: int, n_items: int, n_nets: int) -> int:
         return 4 * words + n_items * n_nets * 16 + (1 << 20)
 
+    @staticmethod
+    def _host_bytes(words: int) -> int:
+        """Pinned host mirror of an arena of `words` (its padding, rounded up)."""
+        return ((4 * (words + 64)) + 255) & ~255
+
     # ---- serving ----
     def serve(self, requests: list[Request]) -> ServeStats:
+        ctx = self.ctx
+        host = self.results == "host"
+        if host:
+            ctx.set_option(_g.GLS_OPT_HOST_MIRROR, 1)
+            gmax = max(r.n_nets for r in self.res.values())
+            goff_buf, glen_buf = _pinned(gmax, np.int64), _pinned(gmax, np.uint32)
+        try:
+            return self._serve(requests, host, goff_buf if host else None, glen_buf if host else None)
+        finally:
+            if host:
+                ctx.set_option(_g.GLS_OPT_HOST_MIRROR, 0)
+
+    def _serve(self, requests: list[Request], host: bool, goff_buf, glen_buf) -> ServeStats:
         ctx = self.ctx
         pending: deque[Request] = deque()
         lock = threading.Lock()
@@ -154,16 +201,16 @@ class Server:
 
         th = threading.Thread(target=arrivals, daemon=True)
         th.start()
-        inflight = []            # (run_id, reqs, stream index, bytes, words)
+        inflight = []            # (run_id, reqs, stream index, device bytes, words, host bytes)
         free_streams = list(range(len(self.streams)))
-        used = 0
+        used = used_host = 0
         launches, items, readmitted = 0, 0, 0
         scale: dict[str, float] = {}
         while True:
             progressed = False
             # retire finished launches
             for entry in list(inflight):
-                rid, reqs, si, nbytes, words = entry
+                rid, reqs, si, nbytes, words, hbytes = entry
                 if not ctx.run_done(rid):
                     continue
                 rc, total, _ = ctx.run_stats_raw(rid)
@@ -183,6 +230,13 @@ class Server:
                     # the launch's gate transitions, shared among its requests
                     share, rem = divmod(total, len(reqs))
                     for i, q in enumerate(reqs):
+                        if host:   # descriptors to host memory: the waveforms are already there
+                            arena, goff, glen = ctx.read_host(rid, i, goff_buf, glen_buf)
+                            now = time.perf_counter()
+                            if self.keep:
+                                q.host_gates = np.concatenate(
+                                    [arena[o:o + n] for o, n in zip(goff.tolist(), glen.tolist())] or
+                                    [np.zeros(0, np.uint32)])
                         q.t_done = now - t0
                         q.out_transitions = share + (rem if i == 0 else 0)
                         if self.keep:
@@ -191,6 +245,7 @@ class Server:
                 inflight.remove(entry)
                 free_streams.append(si)
                 used -= nbytes
+                used_host -= hbytes
                 progressed = True
             # admit waiting requests
             while free_streams:
@@ -216,11 +271,17 @@ class Server:
                 r = self.res[head.netlist]
                 sc = scale.get(head.netlist, 1.0)
                 words = [int(self.estimate_words(q.netlist, q.t_limit) * sc) for q in group]
-                while len(group) > 1 and used + self._footprint(sum(words), len(group), r.n_nets) > self.budget:
+                hb = self.host_budget if host and self.host_budget is not None else None
+                while len(group) > 1 and (used + self._footprint(sum(words), len(group), r.n_nets) > self.budget or
+                                          (hb is not None and used_host + self._host_bytes(sum(words)) > hb)):
                     group.pop()
                     words.pop()
                 need = self._footprint(sum(words), len(group), r.n_nets)
-                if used + need > self.budget and inflight:
+                need_host = self._host_bytes(sum(words)) if host else 0
+                if hb is not None and need_host > hb:
+                    raise GlsError(_g.GLS_ENOMEM, f"request {head.rid} needs a {need_host}-byte host mirror, "
+                                                  f"beyond the {hb}-byte host budget")
+                if (used + need > self.budget or (hb is not None and used_host + need_host > hb)) and inflight:
                     break       # wait for memory
                 si = free_streams.pop()
                 with lock:
@@ -238,8 +299,9 @@ class Server:
                     if not inflight:
                         raise
                     break
-                inflight.append((rid, group, si, need, sum(words)))
+                inflight.append((rid, group, si, need, sum(words), need_host))
                 used += need
+                used_host += need_host
                 launches += 1
                 items += len(group)
                 progressed = True
@@ -256,6 +318,18 @@ class Server:
         return ServeStats(len(requests), wall, float(np.percentile(lat, 50)), float(np.percentile(lat, 99)),
                           float(lat.mean()), tr, tr / max(wall, 1e-9), launches, items / max(1, launches),
                           readmitted, lat.tolist())
+
+
+def _pinned(n: int, dtype):
+    """A page-locked host array of n elements (for the descriptor copies)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            t = torch.empty(max(n, 1) * np.dtype(dtype).itemsize, dtype=torch.uint8).pin_memory()
+            return t.numpy().view(dtype)
+    except ImportError:
+        pass
+    return np.zeros(max(n, 1), dtype)
 
 
 def poisson_trace(n_seconds: float, rate: float, keys: list[str], wmin: int, wmax: int, seed: int) -> list[Request]:

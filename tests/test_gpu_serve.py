@@ -37,6 +37,7 @@ def test_served_results_equal_alone_and_oracle(batching, streams, policy):
     res = residents()
     with gls.Context(0) as ctx:
         ctx.set_option(gls.gls.GLS_OPT_POOL_BYTES, 8 << 30)
+        ctx.set_option(gls.gls.GLS_OPT_HOST_POOL_BYTES, 4 << 30)
         srv = Server(ctx, budget_bytes=4 << 30, max_batch=8, streams=streams, batching=batching,
                      keep_results=True, policy=policy)
         for k, (nl, st) in res.items():
@@ -57,6 +58,8 @@ def test_served_results_equal_alone_and_oracle(batching, streams, policy):
             off, packed = q.result
             t, v = gls.unpack(packed)
             assert_same(oracle.sim_event(nl, _cut(st, q.t_limit)), off, t, v, f"request {q.rid}")
+            # the waveforms the kernels wrote to host memory are the same
+            np.testing.assert_array_equal(q.host_gates, packed[off[nl.n_pi]:])
         # a few requests alone, outside the mix
         for q in trace[:5]:
             r = srv.res[q.netlist]
@@ -97,3 +100,35 @@ def test_pool_reuse_and_coalescing():
         ctx.release(sid)
         ctx.release(nid)
         ctx.set_option(gls.gls.GLS_OPT_POOL_BYTES, 0)
+
+
+def test_host_pool_mirrors():
+    w = synth.make_workload("tiny200", seed=5)
+    ref = oracle.sim_event(w.netlist, w.stimulus)
+    P = w.netlist.n_pi
+    with gls.Context(0) as ctx:
+        ctx.set_option(gls.gls.GLS_OPT_HOST_POOL_BYTES, 64 << 20)
+        ctx.set_option(gls.gls.GLS_OPT_HOST_MIRROR, 1)
+        nid = ctx.load_netlist(w.netlist)
+        sid = ctx.load_stimulus(w.stimulus)
+        # mirrors carved from the pinned pool, released out of order and reused
+        for rnd in range(2):
+            rids = [ctx.simulate(nid, sid, arena_events=1 << 20) for _ in range(4)]
+            for rid in rids[1::2] + rids[::2]:
+                arena, goff, glen = ctx.read_host(rid)
+                gates = np.concatenate([arena[o:o + n] for o, n in zip(goff.tolist(), glen.tolist())])
+                t, v = gls.unpack(gates)
+                np.testing.assert_array_equal(t.astype(np.int64), ref.t[ref.off[P]:])
+                np.testing.assert_array_equal(v, ref.v[ref.off[P]:])
+                ctx.release(rid)
+        # a mirror larger than the pool is refused at run creation
+        with pytest.raises(gls.GlsError) as ei:
+            ctx.simulate(nid, sid, arena_events=(80 << 20) // 4)
+        assert ei.value.code == gls.gls.GLS_ENOMEM
+        # the pool cannot be dropped while a mirror is in use
+        rid = ctx.simulate(nid, sid, arena_events=1 << 20)
+        with pytest.raises(gls.GlsError):
+            ctx.set_option(gls.gls.GLS_OPT_HOST_POOL_BYTES, 0)
+        ctx.release(rid)
+        ctx.set_option(gls.gls.GLS_OPT_HOST_MIRROR, 0)
+        ctx.set_option(gls.gls.GLS_OPT_HOST_POOL_BYTES, 0)

@@ -9,6 +9,8 @@ the oracle, is in test_gpu_serve.py).
 """
 import itertools
 
+import numpy as np
+
 from paper_2304_13398_gb300 import autotune
 from paper_2304_13398_gb300 import gls as G
 from paper_2304_13398_gb300.serve import Request, Server
@@ -24,6 +26,9 @@ class FakeCtx:
         self.runs = {}
         self.launches = []                 # (netlist ids, t_limits, arena words) in launch order
         self.planned = []
+        self.options = {}
+        self.mirror_set = []               # GLS_OPT_HOST_MIRROR values in the order set
+        self.host_reads = []               # (run id, item) of every gls_read_host
 
     def demand(self, items):
         sc = 1.0 if self.calibrating else self.scale
@@ -61,6 +66,16 @@ class FakeCtx:
 
     def plan_order(self, nid, rid=-1, item=0):
         self.planned.append(nid)
+
+    def set_option(self, option, value):
+        self.options[option] = value
+        if option == G.GLS_OPT_HOST_MIRROR:
+            self.mirror_set.append(value)
+
+    def read_host(self, rid, item=0, gate_off=None, gate_len=None):
+        assert self.options.get(G.GLS_OPT_HOST_MIRROR) == 1, "results read from a run without a host mirror"
+        self.host_reads.append((rid, item))
+        return np.zeros(1, np.uint32), np.zeros(0, np.int64), np.zeros(0, np.uint32)
 
     def release(self, rid):
         self.runs.pop(rid, None)
@@ -102,6 +117,16 @@ def test_plain_form_is_fifo_one_request_per_launch():
     assert st.launches == 5 and st.mean_batch == 1.0
     assert [l[1] for l in ctx.launches] == [[900], [100], [500], [300], [700]]
     assert all(q.t_done >= q.arrival for q in reqs)
+    # latency ends with the results in host memory: one descriptor read per
+    # request, from runs created with the host mirror, which is off again after
+    assert len(ctx.host_reads) == 5 and ctx.mirror_set == [1, 0]
+
+
+def test_device_results_skip_the_host_read():
+    ctx = FakeCtx({1: 1.0})
+    srv = make_server(ctx, [1], budget_bytes=1 << 40, batching=False, streams=1, policy="fifo", results="device")
+    st = srv.serve([Request(i, "n1", 500, 0.0005 * i) for i in range(3)])
+    assert st.requests == 3 and ctx.host_reads == [] and ctx.mirror_set == []
 
 
 def test_shortest_job_first():
@@ -214,3 +239,27 @@ def test_autotune_leaves_the_fastest_candidate_applied():
     assert res.best == {"kernel": "wide", "warps_per_cta": 2}
     assert ctx.key()[:2] == ("wide", 2)
     assert len(built) == len(autotune.DEFAULT_CANDIDATES) == len(res.timings_ms)
+
+
+def test_host_mirror_budget_limits_launches_in_flight():
+    # each request's mirror takes about 4 * (1000 * 1.3 + 4096) bytes; a host
+    # budget for one and a half of them keeps one launch in flight at a time
+    ctx = FakeCtx({1: 0.1}, polls=50)
+    one = Server._host_bytes(int(0.1 * 10_000 * 1.3) + 4096)
+    srv = make_server(ctx, [1], budget_bytes=1 << 40, batching=False, streams=4, policy="fifo",
+                      host_budget_bytes=int(1.5 * one))
+    seen = []
+    orig = ctx.simulate_batch
+
+    def counting(*a, **k):
+        seen.append(sum(1 for r in ctx.runs.values() if r["polls"] > 0))
+        return orig(*a, **k)
+    ctx.simulate_batch = counting
+    st = srv.serve([Request(i, "n1", 10_000, 0.0) for i in range(4)])
+    assert st.launches == 4 and max(seen) == 0, "a second mirror was admitted beyond the host budget"
+    # a request whose mirror alone exceeds the budget is refused with a clear error
+    srv.host_budget = one // 2
+    import pytest
+    with pytest.raises(G.GlsError) as ei:
+        srv.serve([Request(0, "n1", 10_000, 0.0)])
+    assert ei.value.code == G.GLS_ENOMEM
