@@ -228,10 +228,10 @@ int gls_run_stats(gls_ctx *ctx, int32_t run_id, int64_t *total_events, double *k
    NULL.  The warps of a run claim the arena in blocks; each gate reserves its
    Eq. 2 bound inside its warp's block while it runs and keeps only its
    waveform (both padded to 128-byte lines), so the demand is the output
-   (padded) plus the unused ends of the blocks -- at most about a sixteenth of
-   the arena, and it varies by that much from run to run with the order in
-   which the warps take the gates.  The demand sizes later runs of similar
-   inputs (the serving admission model). */
+   (padded) plus the unused ends of the blocks (up to a quarter of the arena,
+   at most 1 MiB per warp), and it varies with the order in which the warps
+   take the gates.  The demand sizes later runs of similar inputs (the
+   serving admission model). */
 int gls_run_info(gls_ctx *ctx, int32_t run_id, int64_t *arena_demand, int64_t *arena_capacity);
 
 /*

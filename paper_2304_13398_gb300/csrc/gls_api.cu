@@ -737,12 +737,13 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
     }
     const int64_t N = r->n_nets;
     r->dev.arena_cap = (uint64_t)arena_events;
-    {   // warps claim the arena in blocks of about a sixteenth of their share per
-        // launch (at most 32 Ki words), so the unused block tails stay a few
-        // percent of the arena; below one line every gate claims its own slot
+    {   // warps claim the arena in blocks of a quarter of their share per launch,
+        // at most 256 Ki words (1 MiB): large against a gate's Eq. 2 bound, so
+        // little of a block is left behind when a gate's bound does not fit
+        // its rest; below one line every gate claims its own slot
         const uint64_t warps = (uint64_t)std::max(1, c->cfg.ctas * c->cfg.warps_per_cta);
         const uint64_t launches = r->schedule == GLS_SCHEDULE_DEPENDENCY ? 1 : (uint64_t)std::max(1, r->depth);
-        const uint64_t blk = std::min<uint64_t>((uint64_t)arena_events / (16 * warps * launches), 32768);
+        const uint64_t blk = std::min<uint64_t>((uint64_t)arena_events / (4 * warps * launches), 262144);
         r->dev.arena_blk = (uint32_t)(blk & ~(uint64_t)(kSlotAlign - 1));
     }
     r->dev.n_pi = 0;

@@ -309,24 +309,35 @@ __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0,
     int nf = 0;
     uint32_t outCount = cs.outCount;
     uint32_t vlast = cs.lastV;   // value of the element before this round
-    for (int b0 = 0; b0 < nQ; b0 += 32) {
-        const int idx = b0 + lane;
-        const uint32_t e = idx < nQ ? sm.Q[idx] : 0u;
-        const bool fin = idx < nQ && (e >> 2) < Tfin;
-        const uint32_t up = __shfl_up_sync(FULL, e & 3u, 1);
-        const uint32_t pv = lane == 0 ? vlast : up;
-        vlast = __shfl_sync(FULL, e & 3u, 31);
-        const bool keep = fin && ((e & 3u) != pv);
-        const uint32_t bk = __ballot_sync(FULL, keep);
-        if (keep) {
-            const uint32_t at = outCount + __popc(bk & lanemask_lt);
-            out[at] = e;
-            if (MIRROR) hout[at] = e;   // the host mirror of the store
+    // two batches of 32 per round, independent but for the carried values;
+    // t_r increases along Q, so the final ones are a prefix and the second
+    // batch has none unless the first is all final
+    for (int b0 = 0; b0 < nQ; b0 += 64) {
+        const int i1 = b0 + lane, i2 = b0 + 32 + lane;
+        const uint32_t e1 = i1 < nQ ? sm.Q[i1] : 0u, e2 = i2 < nQ ? sm.Q[i2] : 0u;
+        const bool f1 = i1 < nQ && (e1 >> 2) < Tfin, f2 = i2 < nQ && (e2 >> 2) < Tfin;
+        const uint32_t v1 = e1 & 3u, v2 = e2 & 3u;
+        const uint32_t up1 = __shfl_up_sync(FULL, v1, 1), up2 = __shfl_up_sync(FULL, v2, 1);
+        const uint32_t last1 = __shfl_sync(FULL, v1, 31);
+        const bool k1 = f1 && v1 != (lane == 0 ? vlast : up1);
+        const bool k2 = f2 && v2 != (lane == 0 ? last1 : up2);
+        vlast = __shfl_sync(FULL, v2, 31);
+        const uint32_t bk1 = __ballot_sync(FULL, k1), bk2 = __ballot_sync(FULL, k2);
+        const uint32_t n1 = __popc(bk1);
+        if (k1) {
+            const uint32_t at = outCount + __popc(bk1 & lanemask_lt);
+            out[at] = e1;
+            if (MIRROR) hout[at] = e1;   // the host mirror of the store
         }
-        outCount += __popc(bk);
-        const uint32_t bf = __ballot_sync(FULL, fin);
-        nf += __popc(bf);
-        if (bf != FULL) break;   // the final ones are a prefix: the rest stays pending
+        if (k2) {
+            const uint32_t at = outCount + n1 + __popc(bk2 & lanemask_lt);
+            out[at] = e2;
+            if (MIRROR) hout[at] = e2;
+        }
+        outCount += n1 + __popc(bk2);
+        const uint32_t bf1 = __ballot_sync(FULL, f1), bf2 = __ballot_sync(FULL, f2);
+        nf += __popc(bf1) + __popc(bf2);
+        if ((bf1 & bf2) != FULL) break;   // the rest stays pending
     }
     cs.outCount = outCount;
     if (nf > 0) cs.lastV = sm.Q[nf - 1] & 3u;
