@@ -53,6 +53,7 @@ class Request:
     t_done: float = -1.0
     out_transitions: int = 0
     attempts: int = 0
+    boost: float = 1.0            # growth of its footprint estimate after arena overflows
     result: tuple | None = None   # (off, packed) when the server keeps results
     host_gates: object = None     # with results="host" and kept results: the gates' words from the mirror
 
@@ -65,8 +66,9 @@ class Resident:
     n_nets: int
     pi_events: int
     window: int
-    words_per_event: float = 0.0
-    out_per_event: float = 0.0   # gate-output transitions per stimulus transition (calibration run)
+    words_per_event: float = 0.0  # arena words per stimulus transition of the window (slope)
+    words_fixed: float = 0.0      # arena words of any window (intercept: per-gate slot padding, block ends)
+    out_per_event: float = 0.0    # gate-output transitions per stimulus transition (calibration run)
 
 
 @dataclass
@@ -121,38 +123,51 @@ class Server:
         self.res[key] = Resident(key, nid, sid, int(netlist.n_pi + netlist.n_gates), int(stimulus.n_events),
                                  int(window))
 
-    def calibrate(self, frac: float = 1.0, plan: bool = True):
-        """Event-arena words per stimulus transition of each resident netlist,
-        from one run over the first `frac` of its window (the footprint model
-        of admission; transitions are spread evenly over the window).  The
-        whole window is the default: nets start at X, so the first part of a
-        window carries fewer output transitions per input transition than
-        the rest, and a model taken there would fall short for long windows.
-        With plan, the same run also plans the netlist's critical-path-first
-        gate order for the dependency schedule (gls_plan_order)."""
+    def calibrate(self, frac: float = 1.0, plan: bool = True, short_frac: float = 1e-3):
+        """Footprint model of admission for each resident netlist: arena
+        words = fixed + per_event x (stimulus transitions in the window),
+        fitted to two runs, over the first short_frac and the first frac of
+        the netlist's window (transitions are spread evenly over it).  The
+        fixed part is the per-gate slot padding and the block ends that any
+        window pays; the whole window is the default for the long run
+        because nets start at X, so the first part of a window carries fewer
+        output transitions per input transition than the rest.  With plan,
+        the long run also plans the netlist's critical-path-first gate order
+        for the dependency schedule (gls_plan_order)."""
         for r in self.res.values():
-            t_limit = max(1, int(r.window * frac))
-            arena = 0
-            while True:
-                rid = self.ctx.simulate_batch([r.nid], [r.sid], t_limits=[t_limit], arena_events=arena)
-                rc, demand, _ = self.ctx.run_stats_raw(rid)
-                if rc == 0:
-                    r.out_per_event = demand / max(1.0, r.pi_events * frac)
-                    demand = self.ctx.run_info(rid)[0]
-                    if plan:
-                        self.ctx.plan_order(r.nid, rid)
-                self.ctx.release(rid)
-                if rc == 0:
-                    break
-                if rc != _g.GLS_EOVERFLOW:
-                    raise GlsError(rc, "calibration run failed")
-                arena = int(demand * 1.5) + 4096
-            r.words_per_event = max(1.0, demand / max(1.0, r.pi_events * frac))
+            pts = []
+            for f in ((short_frac, frac) if short_frac < frac else (frac,)):
+                t_limit = max(1, int(r.window * f))
+                arena = 0
+                while True:
+                    rid = self.ctx.simulate_batch([r.nid], [r.sid], t_limits=[t_limit], arena_events=arena)
+                    rc, total, _ = self.ctx.run_stats_raw(rid)
+                    if rc == 0:
+                        demand = self.ctx.run_info(rid)[0]
+                        if f == frac:
+                            r.out_per_event = total / max(1.0, r.pi_events * f)
+                            if plan:
+                                self.ctx.plan_order(r.nid, rid)
+                    self.ctx.release(rid)
+                    if rc == 0:
+                        break
+                    if rc != _g.GLS_EOVERFLOW:
+                        raise GlsError(rc, "calibration run failed")
+                    arena = int(total * 1.5) + 4096
+                pts.append((r.pi_events * f, float(demand)))
+            if len(pts) == 2 and pts[1][0] > pts[0][0]:
+                (e1, d1), (e2, d2) = pts
+                r.words_per_event = max(0.0, (d2 - d1) / (e2 - e1))
+                r.words_fixed = max(0.0, d1 - r.words_per_event * e1)
+            else:
+                e2, d2 = pts[-1]
+                r.words_per_event = max(1.0, d2 / max(1.0, e2))
+                r.words_fixed = 0.0
 
     def estimate_words(self, key: str, t_limit: int) -> int:
         r = self.res[key]
         frac = min(1.0, max(t_limit, 1) / r.window)
-        return int(r.words_per_event * r.pi_events * frac * self.safety) + 4096
+        return int((r.words_fixed + r.words_per_event * r.pi_events * frac) * self.safety) + 4096
 
     def expected_transitions(self, key: str, t_limit: int) -> float:
         """Gate-output transitions a request is expected to produce (the
@@ -205,7 +220,6 @@ class Server:
         free_streams = list(range(len(self.streams)))
         used = used_host = 0
         launches, items, readmitted = 0, 0, 0
-        scale: dict[str, float] = {}
         while True:
             progressed = False
             # retire finished launches
@@ -216,12 +230,12 @@ class Server:
                 rc, total, _ = ctx.run_stats_raw(rid)
                 now = time.perf_counter()
                 if rc == _g.GLS_EOVERFLOW:
-                    # the estimate was too small: grow this netlist's model and re-admit
-                    key = reqs[0].netlist
-                    scale[key] = scale.get(key, 1.0) * max(2.0, 1.2 * total / max(1, words))
+                    # the estimate was too small for these requests: grow theirs and re-admit
+                    grow = max(2.0, 1.2 * total / max(1, words))
                     with lock:
                         for q in reversed(reqs):
                             q.attempts += 1
+                            q.boost *= grow
                             pending.appendleft(q)
                     readmitted += len(reqs)
                 elif rc != 0:
@@ -269,8 +283,7 @@ class Server:
                             if q is not head and q.netlist == head.netlist:
                                 group.append(q)
                 r = self.res[head.netlist]
-                sc = scale.get(head.netlist, 1.0)
-                words = [int(self.estimate_words(q.netlist, q.t_limit) * sc) for q in group]
+                words = [int(self.estimate_words(q.netlist, q.t_limit) * q.boost) for q in group]
                 hb = self.host_budget if host and self.host_budget is not None else None
                 while len(group) > 1 and (used + self._footprint(sum(words), len(group), r.n_nets) > self.budget or
                                           (hb is not None and used_host + self._host_bytes(sum(words)) > hb)):

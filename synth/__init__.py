@@ -29,7 +29,7 @@ ALL_CELLS = (1 << len(CELLS)) - 1
 def build(force: bool = False) -> str:
     """Compile libsynth.so in place (plain gcc, no GPU needed)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
                                "-o", _LIB + ".tmp", _SRC, "-lm"])
         os.replace(_LIB + ".tmp", _LIB)
     return _LIB

@@ -268,6 +268,8 @@ int64_t synth_stim_counts(int32_t n_pi, uint64_t seed, double mean, int64_t wind
                           int32_t n_clock, int32_t clock_period, int32_t clock_trans, int64_t *counts) {
     stim_cfg c; make_cfg(&c, n_pi, seed, mean, window, p0, p1, px, pz, n_clock, clock_period, clock_trans);
     int64_t tot = 0;
+    /* every PI draws from its own stream, so the PIs are independent */
+    #pragma omp parallel for schedule(dynamic, 64) reduction(+:tot)
     for (int32_t i = 0; i < n_pi; i++) { counts[i] = gen_pi(&c, i, NULL, NULL, NULL); tot += counts[i]; }
     return tot;
 }
@@ -277,11 +279,13 @@ int synth_stim_fill64(int32_t n_pi, uint64_t seed, double mean, int64_t window,
                       int32_t n_clock, int32_t clock_period, int32_t clock_trans,
                       const int64_t *off, int64_t *t, uint8_t *v) {
     stim_cfg c; make_cfg(&c, n_pi, seed, mean, window, p0, p1, px, pz, n_clock, clock_period, clock_trans);
+    int bad = 0;
+    #pragma omp parallel for schedule(dynamic, 64) reduction(|:bad)
     for (int32_t i = 0; i < n_pi; i++) {
         int64_t n = gen_pi(&c, i, NULL, t + off[i], v + off[i]);
-        if (n != off[i + 1] - off[i]) return -1;
+        if (n != off[i + 1] - off[i]) bad = 1;
     }
-    return 0;
+    return bad ? -1 : 0;
 }
 /* synth_stim_fill: the transitions themselves, PI i at [off[i], off[i+1]) */
 int synth_stim_fill(int32_t n_pi, uint64_t seed, double mean, int64_t window,
@@ -289,9 +293,11 @@ int synth_stim_fill(int32_t n_pi, uint64_t seed, double mean, int64_t window,
                     int32_t n_clock, int32_t clock_period, int32_t clock_trans,
                     const int64_t *off, int32_t *t, uint8_t *v) {
     stim_cfg c; make_cfg(&c, n_pi, seed, mean, window, p0, p1, px, pz, n_clock, clock_period, clock_trans);
+    int bad = 0;
+    #pragma omp parallel for schedule(dynamic, 64) reduction(|:bad)
     for (int32_t i = 0; i < n_pi; i++) {
         int64_t n = gen_pi(&c, i, t + off[i], NULL, v + off[i]);
-        if (n != off[i + 1] - off[i]) return -1;
+        if (n != off[i + 1] - off[i]) bad = 1;
     }
-    return 0;
+    return bad ? -1 : 0;
 }

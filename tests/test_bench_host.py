@@ -58,3 +58,17 @@ def test_recorded_traffic_only_for_its_own_configuration():
 
 def test_cpu_model_names_something():
     assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
+
+
+def test_trace_copies_are_fresh_requests():
+    from paper_2304_13398_gb300.serve import Request
+    tr = [Request(0, "n0", 5000, 0.1), Request(1, "n1", 7000, 0.2)]
+    tr[0].t_done, tr[0].out_transitions = 1.0, 99
+    cp = bench.copy_trace(tr)
+    assert [(q.rid, q.netlist, q.t_limit, q.arrival) for q in cp] == [(0, "n0", 5000, 0.1), (1, "n1", 7000, 0.2)]
+    assert all(q.t_done < 0 and q.out_transitions == 0 for q in cp) and cp[0] is not tr[0]
+
+
+def test_mem_available_reads_meminfo():
+    m = bench.mem_available_bytes()
+    assert m > 0 and m % 1024 == 0

@@ -94,7 +94,7 @@ def make_server(ctx, nets, window=10_000, **kw):
     srv = Server(ctx, stream_factory=object, **kw)
     for n in nets:
         srv.add_resident(f"n{n}", Net(n), Stim(), window)
-    srv.calibrate(frac=0.2)
+    srv.calibrate()
     ctx.calibrating = False
     return srv
 
@@ -103,10 +103,12 @@ def test_calibration_fits_the_footprint_model_and_plans_orders():
     ctx = FakeCtx({1: 2.0, 2: 0.5})
     srv = make_server(ctx, [1, 2], budget_bytes=1 << 40)
     assert sorted(ctx.planned) == [1, 2]
-    # words per stimulus transition x transitions in the window, with the safety factor
+    # the fake's demand is proportional to the window: the two-point fit finds
+    # no fixed part, and the estimate is the demand with the safety factor
     for nid, wpp in ((1, 2.0), (2, 0.5)):
+        assert abs(srv.res[f"n{nid}"].words_fixed) < 1e-6
         est = srv.estimate_words(f"n{nid}", 10_000)
-        assert est == int(wpp * 10_000 * srv.safety) + 4096
+        assert abs(est - (int(wpp * 10_000 * srv.safety) + 4096)) <= 1
 
 
 def test_plain_form_is_fifo_one_request_per_launch():
@@ -263,3 +265,22 @@ def test_host_mirror_budget_limits_launches_in_flight():
     with pytest.raises(G.GlsError) as ei:
         srv.serve([Request(0, "n1", 10_000, 0.0)])
     assert ei.value.code == G.GLS_ENOMEM
+
+
+def test_footprint_model_has_a_fixed_part():
+    # demand = 50,000 words of any window (slot padding, block ends) + 2 words per ps
+    class FixedCtx(FakeCtx):
+        def demand(self, items):
+            sc = 1.0 if self.calibrating else self.scale
+            return int(sum(50_000 + self.wpp[n] * t for n, t in items) * sc)
+    ctx = FixedCtx({1: 2.0})
+    srv = make_server(ctx, [1], budget_bytes=1 << 40)
+    r = srv.res["n1"]
+    assert abs(r.words_fixed - 50_000) <= 2 and abs(r.words_per_event - 20.0) < 0.01
+    # a short window is estimated above its demand (a purely proportional
+    # model would give it about 2% of it), a long one too
+    for t in (10, 1_000, 10_000):
+        assert srv.estimate_words("n1", t) >= ctx.demand([(1, t)])
+    # served without overflow
+    st = srv.serve([Request(i, "n1", t, 0.0) for i, t in enumerate((10, 100, 5_000, 10_000))])
+    assert st.readmitted == 0 and st.requests == 4
