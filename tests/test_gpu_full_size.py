@@ -35,9 +35,18 @@ def test_ind1m_every_gate_and_invariants():
             rc, demand, _ = ctx.run_stats_raw(rid)
         assert rc == 0
         total = ctx.run_stats(rid).total_events
+        demand, _ = ctx.run_info(rid)
         off, packed = ctx.read_all(rid)
     G, P = nl.n_gates, nl.n_pi
     assert total == int(off[-1] - off[P])
+    # the warps' arena blocks keep each slot at its waveform's length: the
+    # arena claimed stays well below the gates' Eq. 2 bounds (the sum of their
+    # fanin lengths, in whole 128-byte lines) and above the output itself
+    lens = np.diff(off)
+    bounds = np.add.reduceat(lens[nl.fanin_net], nl.fanin_off[:-1]) if G else np.zeros(0, np.int64)
+    bounds = np.where(np.diff(nl.fanin_off) > 0, bounds, 0)
+    reserved = int(((bounds + 31) // 32 * 32).sum())
+    assert total <= demand < 0.75 * reserved, (total, demand, reserved)
     # the primary inputs come back as given
     np.testing.assert_array_equal(np.diff(off[:P + 1]), np.diff(st.off))
     v = (packed & 3).astype(np.uint8)
