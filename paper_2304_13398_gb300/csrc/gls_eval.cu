@@ -65,7 +65,12 @@ template <int CH>
 struct __align__(16) WarpSmem {
     static constexpr int WIN = CH + 8;     // aligned lead (<= 3) + CH + sentinel, multiple of 4
     uint32_t win[1][3][WIN];  // pin windows (refilled while the chunk's survivors are committed)
-    uint32_t cand[3 * CH];    // per-lane stacks of scheduled transitions (t_r << 2 | v)
+    // per-lane stacks of scheduled transitions (t_r << 2 | v), column by
+    // column: entry k of lane l at cand[32 k + l] (cslot), so that the lanes'
+    // pushes, pops and reads fall into distinct banks; a lane's share of a
+    // chunk holds at most 3 CH / 32 transitions, hence at most that many
+    // entries
+    uint32_t cand[3 * CH];
     // Q: carried transitions (front, at most PCAP) + this chunk's survivors
     // (at most 3 CH).  The survivors are written only after the walk, so the
     // part past PCAP also holds the 3-input cells' merged pins a+b during the
@@ -104,6 +109,9 @@ struct __align__(16) WarpSmem {
 struct WarpArena {
     unsigned long long cur, end;
 };
+
+// Word of stack entry k of a lane (column-major per-lane stacks).
+__device__ __forceinline__ int cslot(int k, int lane) { return (k << 5) + lane; }
 
 // Running state of one gate's output between chunks.
 struct CommitState {
@@ -264,16 +272,16 @@ __device__ __forceinline__ bool issue_windows(WarpSmem<CH> &sm, int b, const Gat
     return total > 0;
 }
 
-// Steps 4 and 5 of a chunk, shared by every pin count.  Lane l's stack is
-// cand[d0, top).  Returns false when more than PCAP transitions would be
-// carried.
+// Steps 4 and 5 of a chunk, shared by every pin count.  Lane l's stack
+// holds top - d0 entries (cand[cslot(0, l)] at the bottom).  Returns false
+// when more than PCAP transitions would be carried.
 template <int CH, bool MIRROR>
 __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0, int top, uint32_t Tfin, uint32_t *out,
                                           uint32_t *hout, CommitState &cs) {
     const uint32_t lanemask_lt = (1u << lane) - 1u;
     // Eq. 1 across lanes (suffix minimum of the later lanes' smallest t_r)
     // and against the carried transitions (minimum over the whole chunk)
-    const uint32_t mn = top > d0 ? (sm.cand[d0] >> 2) : kTimeInf;
+    const uint32_t mn = top > d0 ? (sm.cand[cslot(0, lane)] >> 2) : kTimeInf;
     uint32_t inc = mn;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -283,7 +291,7 @@ __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0,
     uint32_t after = __shfl_down_sync(FULL, inc, 1);
     if (lane == 31) after = kTimeInf;
     const uint32_t Mall = __shfl_sync(FULL, inc, 0);
-    while (top > d0 && (sm.cand[top - 1] >> 2) >= after) top--;
+    while (top > d0 && (sm.cand[cslot(top - 1 - d0, lane)] >> 2) >= after) top--;
     const int np = cs.np;
     int npk = 0;
     for (int b0 = 0; b0 < np; b0 += 32) {
@@ -302,7 +310,7 @@ __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0,
     const int pos = npk + (int)(pre - cnt);
     __syncwarp();
 #pragma unroll 4
-    for (uint32_t x = 0; x < cnt; x++) sm.Q[pos + x] = sm.cand[d0 + x];
+    for (uint32_t x = 0; x < cnt; x++) sm.Q[pos + x] = sm.cand[cslot((int)x, lane)];
     const int nQ = npk + total;
     __syncwarp();
     // commit the final prefix (t_r < Tfin), dropping repeats (Fig. 6)
@@ -605,8 +613,8 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         int top = d0;
         // The walks are branch-free apart from the Eq. 1 pop loop: state
         // updates are selects, the stack top sits in a register, and a
-        // candidate is always written one slot above the stack top (scratch
-        // inside the lane's share) and kept by advancing the top.
+        // candidate is always written one entry above the stack top (scratch
+        // inside the lane's column) and kept by advancing the top.
         if (K == 1) {
             // one pin: every transition is its own timestamp
             uint32_t vprev = d0 > 0 ? (L[d0 - 1] & 3u) : (carry & 3u);   // pin value before the share
@@ -627,9 +635,9 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
                 const uint32_t key = (t + dl) << 2;
                 while (chg && top > d0 && topv >= key) {
                     top--;
-                    topv = top > d0 ? sm.cand[top - 1] : 0u;
+                    topv = top > d0 ? sm.cand[cslot(top - 1 - d0, lane)] : 0u;
                 }
-                sm.cand[top] = key | F;
+                sm.cand[cslot(top - d0, lane)] = key | F;
                 top += chg;
                 topv = chg ? (key | F) : topv;
                 Fprev = F;
@@ -716,9 +724,9 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
                 const bool chg = end && F != Fprev;
                 while (chg && top > d0 && topv >= key) {
                     top--;
-                    topv = top > d0 ? sm.cand[top - 1] : 0u;
+                    topv = top > d0 ? sm.cand[cslot(top - 1 - d0, lane)] : 0u;
                 }
-                sm.cand[top] = key | F;
+                sm.cand[cslot(top - d0, lane)] = key | F;
                 top += chg;
                 topv = chg ? (key | F) : topv;
                 Fprev = end ? F : Fprev;
