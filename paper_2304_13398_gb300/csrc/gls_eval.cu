@@ -557,8 +557,11 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         } else {
             // m[p] = transitions of window p at or before Tend (a prefix):
             // count the S-blocks whose last transition qualifies, then the
-            // qualifying transitions of the first block that does not
-            constexpr int S = WarpSmem<CH>::template chunk<K>() / 32;
+            // qualifying transitions of the first block that does not (its
+            // last one does not qualify, so S - 1 <= 32 tests suffice).  S is
+            // odd, so the 32 block ends fall into 32 different banks.
+            constexpr int S = ((WarpSmem<CH>::template chunk<K>() + 31) / 32) | 1;
+            static_assert(32 * S >= WarpSmem<CH>::template chunk<K>() && S <= 33, "cut blocks");
             int q[3];
 #pragma unroll
             for (int p = 0; p < K; p++) {
