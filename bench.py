@@ -467,8 +467,8 @@ def run_own(a):
         e2e = {"value": all_out / (e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "link": link,
                "timing": "host wall clock over the public calls, pinned host buffers",
-               "result_path": "gls_read_host: the kernels store every output transition into a pinned host "
-                              "mirror as they go; the step ends when all waveforms and their descriptors are "
+               "result_path": "gls_read_host: the kernels copy every gate waveform into a pinned host "
+                              "mirror as each gate finishes; the step ends when all waveforms and their descriptors are "
                               "in host memory (primary inputs are the caller's stimulus)"}
 
     # `config` names the workload only (the reference arm prints the same

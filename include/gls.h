@@ -405,9 +405,10 @@ typedef enum gls_option {
     GLS_OPT_SEGMENT = 6,        /* segmented kernel: input transitions per lane segment, >= 1
                                    (default 32); a gate uses min(32, ceil(inputs / this)) lanes */
     GLS_OPT_HOST_MIRROR = 8,    /* 1: runs created afterwards (not sliced, windowed kernels)
-                                   also store every output transition into a pinned host mirror
-                                   of their event arena as the kernels write it, so the results
-                                   reach host memory while the simulation runs (gls_read_host);
+                                   also copy every gate's waveform into a pinned host mirror of
+                                   their event arena as soon as the gate is done (aligned 16-byte
+                                   stores), so the results reach host memory while the
+                                   simulation runs (gls_read_host);
                                    0 (default): results stay on the device until read */
     GLS_OPT_POOL_BYTES = 7,     /* > 0: allocate one device region of this size now and carve
                                    every later netlist, stimulus and run buffer from it (first

@@ -335,12 +335,10 @@ __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0,
         if (k1) {
             const uint32_t at = outCount + __popc(bk1 & lanemask_lt);
             out[at] = e1;
-            if (MIRROR) hout[at] = e1;   // the host mirror of the store
         }
         if (k2) {
             const uint32_t at = outCount + n1 + __popc(bk2 & lanemask_lt);
             out[at] = e2;
-            if (MIRROR) hout[at] = e2;
         }
         outCount += n1 + __popc(bk2);
         const uint32_t bf1 = __ballot_sync(FULL, f1), bf2 = __ballot_sync(FULL, f2);
@@ -768,6 +766,16 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
             uint32_t *pp = r.pend_out + (size_t)out_net * PCAP;
             for (int x = lane; x < cs.np; x += 32) pp[x] = sm.Q[x];
         }
+    }
+    if (MIRROR && !failed && cs.outCount > 0) {
+        // the waveform to the pinned host mirror in whole, aligned 16-byte
+        // words (the slot is line-aligned and padded, so the rounded-up copy
+        // stays inside it); the lanes' stores precede it through the barrier
+        __syncwarp();
+        const uint32_t n16 = (cs.outCount + 3u) >> 2;
+        const uint4 *src = reinterpret_cast<const uint4 *>(out);
+        uint4 *dst = reinterpret_cast<uint4 *>(hout);
+        for (uint32_t x = (uint32_t)lane; x < n16; x += 32) dst[x] = __ldcg(src + x);
     }
     if (lane == 0) {
         if (failed) atomicOr(r.status, kStPendingOverflow);
