@@ -1222,10 +1222,10 @@ __global__ void __maxnreg__(V == kVariantWindowed ? 72 : GLS_WIDE_MAXNREG) depen
             r.net_len[gr.out_net] = 0;
         }
         // publish: this lane's output stores are ordered for the readers' bulk
-        // copies (async proxy) and, through the warp barrier and lane 0's
-        // release, for their acquire of the completion flag
+        // copies (async proxy) and, through the warp barrier (which orders the
+        // lanes' memory accesses among them) and lane 0's release (cumulative
+        // at GPU scope), for their acquire of the completion flag
         fence_proxy_async_global();
-        __threadfence();
         __syncwarp();
         if (lane == 0 && g != r.withhold_gate) st_release(r.done + gr.out_net, 1u);
     }

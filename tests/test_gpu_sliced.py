@@ -2,10 +2,14 @@
 slices equal the CPU oracle's unsliced waveforms transition by transition --
 for slices shorter than a gate delay, around the delays, and longer than the
 whole stimulus; on 64-bit times past 2^32 ps; with an arena too small for a
-slice (re-evaluated with a larger one); and after a rerun."""
+slice (re-evaluated with a larger one); and after a rerun; in a planned
+gate order; and at 20,000 gates of the benchmark recipe's shape."""
+import os
+
 import numpy as np
 import pytest
 
+import bench
 import oracle
 import paper_2304_13398_gb300 as gls
 import synth
@@ -125,3 +129,42 @@ def test_sliced_rejections():
             ctx.simulate_sliced(nid, sid, (1 << 30) - 10)   # slice + longest path reaches 2^30
         with pytest.raises(gls.GlsError):
             ctx.simulate_sliced(nid, sid, 0)
+
+
+@pytest.mark.parametrize("slice_ps", [61, 2_000])
+def test_sliced_planned_order_equals_oracle(slice_ps):
+    """The slices of a launch in a planned (critical-path-first) gate order,
+    as the benchmark runs them; then a rerun of the same run."""
+    nl, st = case(seed=91)
+    ref = oracle.sim_event(nl, st)
+    with gls.Context(0) as ctx:
+        ctx.set_kernel("wide")
+        nid = ctx.load_netlist(nl)
+        sid = ctx.load_stimulus(st)
+        rid = ctx.simulate(nid, sid)
+        ctx.run_stats(rid)
+        ctx.plan_order(nid, rid)
+        ctx.release(rid)
+        rid = ctx.simulate_sliced(nid, sid, slice_ps)
+        off, t, v = ctx.read_all64(rid)
+        assert_same(ref, off, t, v, f"planned, slice {slice_ps}")
+        ctx.rerun(rid)
+        off, t, v = ctx.read_all64(rid)
+        assert_same(ref, off, t, v, f"planned rerun, slice {slice_ps}")
+
+
+def test_sliced_mid_size_industrial_shape():
+    """20,000 gates of the 1M-gate recipe's distributions (depth 26, 400 PIs
+    at 2,000 transitions each over 1e7 ps) in ten 1e6 ps slices, all in one
+    launch, planned order: every waveform against the levelized oracle."""
+    nl, st, net, stim = bench.make_scaled(20_000, 5)
+    ref = oracle.sim_levelized(nl, st, nthreads=os.cpu_count() or 1)
+    with gls.Context(0) as ctx:
+        nid = ctx.load_netlist(nl)
+        bench.plan_from_calibration(ctx, nid, nl, stim, 5)
+        sid = ctx.load_stimulus(st)
+        rid = ctx.simulate_sliced(nid, sid, 1_000_000)
+        assert ctx.run_slices(rid) == int(st.t.max()) // 1_000_000 + 1
+        off, t, v = ctx.read_all64(rid)
+        assert_same(ref, off, t, v, "20k gates, 1e6 ps slices")
+        assert ctx.run_stats(rid).total_events == int(ref.off[-1] - ref.off[nl.n_pi])
