@@ -336,10 +336,16 @@ int gls_load_netlist_cells(gls_ctx *ctx, int32_t n_pi, int32_t n_cells, const in
  * values, its last output value, and the transitions it has scheduled at or
  * after the boundary, which later inputs may still cancel by Eq. 1).  A
  * transition scheduled before a boundary is final then, so the slices'
- * outputs, concatenated, are exactly the unsliced waveforms.  Each slice's
- * waveforms are copied to host memory as the slice completes; device memory
- * holds one slice's transitions, the stimulus and 2 * (4 + 4 * 256) bytes of
- * gate state per net.
+ * outputs, concatenated, are exactly the unsliced waveforms.  Under the
+ * dependency schedule one launch evaluates up to 64 consecutive slices
+ * (GLS_OPT_SLICE_GROUP): once a gate's fanins are done for all of them, one
+ * warp takes the gate through them in turn, carrying its state from each
+ * slice to the next, so the per-gate costs (work claim, record, fanin waits,
+ * completion flag) are paid once per launch.  Under the level schedule each
+ * slice is one set of level launches.  The waveforms of a launch's slices are
+ * copied to host memory once the launch completes; device memory holds one
+ * launch's transitions, the stimulus, 12 bytes of descriptors per net and
+ * slice of a launch, and 3 * (4 + 4 * 256) bytes of gate state per net.
  */
 
 /* Load a stimulus with 64-bit times: like gls_load_stimulus, with
@@ -353,9 +359,10 @@ int gls_load_stimulus64(gls_ctx *ctx, int32_t n_pi, const int64_t *off, const in
  * slice_ps picoseconds; synchronous: returns once every slice is evaluated and
  * copied to host memory.  The last slice runs to the end of all activity.
  * The windowed kernels only (GLS_EINVAL with GLS_KERNEL_SEGMENTED); either
- * schedule and a planned order apply.  arena_events sizes one slice's event
- * arena (0: about 256 words per stimulus transition of an average slice); a
- * slice that overflows it is evaluated again with a larger arena.
+ * schedule and a planned order apply.  arena_events sizes the event arena of
+ * one launch (0: about 256 words per stimulus transition of the slices of a
+ * launch); a launch that overflows it is evaluated again, from the same
+ * input state, with a larger arena.
  * GLS_ERANGE when slice_ps + the longest path delay reaches 2^30 - 1, or when a
  * gate carries more than 256 scheduled transitions across a boundary;
  * GLS_EINVAL for more than 2^20 slices.  gls_run_stats reports the total
@@ -415,12 +422,14 @@ typedef enum gls_option {
                                    fit, no cudaMalloc/cudaFree per run, so creating and freeing
                                    runs does not synchronise the device); 0: free the pool.
                                    Only when no pool block is in use. */
-    GLS_OPT_HOST_POOL_BYTES = 9 /* > 0: allocate one pinned, device-mapped host region of this
+    GLS_OPT_HOST_POOL_BYTES = 9, /* > 0: allocate one pinned, device-mapped host region of this
                                    size now and carve the host mirrors of later runs
                                    (GLS_OPT_HOST_MIRROR) from it, first fit, instead of pinning
                                    new host memory per run; GLS_ENOMEM at run creation when no
                                    block is large enough.  0: free it.  Only when no mirror is
                                    in use. */
+    GLS_OPT_SLICE_GROUP = 10    /* sliced runs under the dependency schedule: most time slices
+                                   one launch evaluates, 1..64 (default 64) */
 } gls_option;
 
 /* Gate kernel variants; all compute the same waveforms.

@@ -337,9 +337,12 @@ struct RunObj {
     int64_t glen_cap = 0;
     // time-sliced runs (task division over time)
     int64_t slice_ps = 0;               // 0: not sliced
-    uint32_t *d_slice_packed = nullptr; // one slice's primary-input transitions
-    uint32_t *d_st[2] = {nullptr, nullptr};    // gate state at slice boundaries (double-buffered)
-    uint32_t *d_pend[2] = {nullptr, nullptr};  // pending transitions, kPendCap per net
+    int32_t slice_group = 1;            // most slices one launch evaluates
+    int32_t launch_slices = 1;          // slices the last launch evaluated (descriptor sets to count)
+    uint32_t *d_slice_packed = nullptr; // primary-input transitions of one launch's slices
+    uint32_t *d_st[3] = {nullptr, nullptr, nullptr};    // gate state at slice boundaries: a launch's
+                                                        // input and the two it alternates between
+    uint32_t *d_pend[3] = {nullptr, nullptr, nullptr};  // pending transitions, kPendCap per net
     struct Slice {
         int64_t t0;                     // start of the slice (local time 0)
         std::vector<int64_t> off;       // [n_nets + 1] caller net order
@@ -370,6 +373,7 @@ struct gls_ctx {
     uint64_t wait_limit_ns = 10ull * 1000 * 1000 * 1000;
     int32_t withhold_gate = -1;
     uint32_t seg_target = 32;
+    int32_t slice_group = kMaxSliceGroup;   // GLS_OPT_SLICE_GROUP
     bool host_mirror = false;           // GLS_OPT_HOST_MIRROR
     int32_t next_id = 1;
     std::unordered_map<int32_t, std::unique_ptr<NetlistObj>> netlists;
@@ -522,7 +526,7 @@ void free_run(gls_ctx *c, RunObj *r) {
     dfree(c, r->d_slice_packed);
     dfree(c, r->d_glen);
     if (r->h_arena && !pool_give(c->hpool, r->h_arena)) cudaFreeHost(r->h_arena);
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < 3; k++) {
         dfree(c, r->d_st[k]);
         dfree(c, r->d_pend[k]);
     }
@@ -728,14 +732,25 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
         uint64_t meta = (uint64_t)r->n_nets * 16 + (uint64_t)r->depth * 4 + 4096;
         uint64_t cap = left > meta ? (left - meta) / 2 / 4 : 0;
         uint64_t want = 256ull * (uint64_t)stim_events + (1ull << 20);
-        if (slice_ps > 0) {   // about one slice's share; a slice that overflows is rerun with more
+        if (slice_ps > 0) {   // about one launch's share; a launch that overflows is rerun with more
             const StimObj *s = find_stim(c, stim_ids[0]);
             const int64_t mt = s->wide ? s->max_time64 : (int64_t)s->max_time;
-            want = 256ull * (uint64_t)(stim_events / (mt / slice_ps + 1) + 1) + (1ull << 20);
+            const int64_t ns = mt / slice_ps + 1;
+            const int64_t per = std::min<int64_t>(ns, r->schedule == GLS_SCHEDULE_DEPENDENCY ? c->slice_group : 1);
+            want = 256ull * (uint64_t)(stim_events / ns + 1) * (uint64_t)per + (1ull << 20);
         }
         arena_events = (int64_t)std::min(cap, want);
     }
     const int64_t N = r->n_nets;
+    if (slice_ps > 0 && r->schedule == GLS_SCHEDULE_DEPENDENCY) {
+        // a warp evaluates its gate over up to slice_group slices per launch
+        // (a descriptor set per slice)
+        const StimObj *s = find_stim(c, stim_ids[0]);
+        const int64_t mt = s->wide ? s->max_time64 : (int64_t)s->max_time;
+        const int64_t ns = s->n_events > 0 ? mt / slice_ps + 1 : 1;
+        r->slice_group = (int32_t)std::max<int64_t>(1, std::min<int64_t>(ns, c->slice_group));
+    }
+    const int64_t NS = N * r->slice_group;   // descriptors of one launch
     r->dev.arena_cap = (uint64_t)arena_events;
     {   // warps claim the arena in blocks of a quarter of their share per launch,
         // at most 256 Ki words (1 MiB): large against a gate's Eq. 2 bound, so
@@ -751,8 +766,8 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
     r->dev.wait_limit_ns = c->wait_limit_ns;
     r->dev.withhold_gate = c->withhold_gate;
     r->dev.seg_target = c->seg_target;
-    rc = dalloc_n(c, &r->dev.net_ptr, (size_t)std::max<int64_t>(N, 1));
-    if (!rc) rc = dalloc_n(c, &r->dev.net_len, (size_t)std::max<int64_t>(N, 1));
+    rc = dalloc_n(c, &r->dev.net_ptr, (size_t)std::max<int64_t>(NS, 1));
+    if (!rc) rc = dalloc_n(c, &r->dev.net_len, (size_t)std::max<int64_t>(NS, 1));
     // padded by one slot line: readers round a waveform's end up to 4 words
     if (!rc) rc = dalloc_n(c, &r->dev.arena, (size_t)arena_events + 2 * kSlotAlign);
     if (!rc) rc = dalloc_n(c, &r->dev.arena_top, 1);
@@ -794,8 +809,8 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
     }
     if (slice_ps > 0) {
         const StimObj *s = find_stim(c, stim_ids[0]);
-        rc = dalloc_n(c, &r->d_slice_packed, (size_t)stim_words(s->cap_events, s->n_pi));
-        for (int k = 0; k < 2 && !rc; k++) {
+        rc = dalloc_n(c, &r->d_slice_packed, (size_t)slice_words(s->cap_events, s->n_pi, r->slice_group));
+        for (int k = 0; k < 3 && !rc; k++) {
             rc = dalloc_n(c, &r->d_st[k], (size_t)std::max<int64_t>(N, 1));
             if (!rc) rc = dalloc_n(c, &r->d_pend[k], (size_t)std::max<int64_t>(N, 1) * kPendCap);
         }
@@ -813,11 +828,15 @@ int create_run(gls_ctx *c, const int32_t *netlist_ids, const int32_t *stim_ids, 
 }
 
 // Dense CSR of one instance of a run (its nets in caller order) into host memory.
-int read_item(gls_ctx *c, RunObj *r, int32_t item, int64_t *off, uint32_t *packed, int64_t cap) {
+// (net_shift: the descriptor set of slice j of a launch over several time
+// slices)
+int read_item(gls_ctx *c, RunObj *r, int32_t item, int64_t *off, uint32_t *packed, int64_t cap,
+              int64_t net_shift = 0) {
     if (item < 0 || item >= (int32_t)r->items.size()) return fail(GLS_EINVAL, "item %d out of range", item);
     const RunItem &it = r->items[item];
     NetlistObj *n = find_netlist(c, it.netlist_id);
     const int64_t N = (int64_t)n->n_pi + n->n_gates;
+    const int64_t net_base = it.net_base + net_shift;
     CK(cudaEventSynchronize(r->ev1));
     int rc = GLS_OK;
     if (r->off_cap < N + 1) {
@@ -832,7 +851,7 @@ int read_item(gls_ctx *c, RunObj *r, int32_t item, int64_t *off, uint32_t *packe
         if (rc) return rc;
         r->off_cap = N + 1;
     }
-    CK(launch_gather_lengths(r->dev.net_len, n->d_ext2int, N, r->d_off, c->stream, it.net_base));
+    CK(launch_gather_lengths(r->dev.net_len, n->d_ext2int, N, r->d_off, c->stream, net_base));
     CK(launch_exclusive_scan_i64(r->d_off, N + 1, r->d_scan_tmp, r->scan_tmp, c->stream));
     CK(cudaMemcpyAsync(off, r->d_off, sizeof(int64_t) * (size_t)(N + 1), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -849,7 +868,7 @@ int read_item(gls_ctx *c, RunObj *r, int32_t item, int64_t *off, uint32_t *packe
         r->gather_cap = total;
     }
     CK(launch_gather_events(r->dev.net_ptr, r->dev.net_len, n->d_ext2int, r->d_off, N, r->d_gather, c->stream,
-                            it.net_base));
+                            net_base));
     CK(cudaMemcpyAsync(packed, r->d_gather, sizeof(uint32_t) * (size_t)total, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return GLS_OK;
@@ -1286,7 +1305,7 @@ int run_stats_impl(gls_ctx *c, RunObj *r, int64_t *total_events, double *kernel_
     CK(cudaMemcpyAsync(&status, r->dev.status, sizeof status, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&top, r->dev.arena_top, sizeof top, cudaMemcpyDeviceToHost, c->stream));
     // every net, minus the primary inputs (their transitions within the time limits)
-    CK(launch_sum_gate_lengths(r->dev.net_len, 0, r->n_nets, r->d_sum, c->stream));
+    CK(launch_sum_gate_lengths(r->dev.net_len, 0, r->n_nets * r->launch_slices, r->d_sum, c->stream));
     unsigned long long pi_events = 0;
     CK(cudaMemcpyAsync(&pi_events, r->d_pi_total, sizeof pi_events, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&sum, r->d_sum, sizeof sum, cudaMemcpyDeviceToHost, c->stream));
@@ -1310,15 +1329,20 @@ int run_stats_impl(gls_ctx *c, RunObj *r, int64_t *total_events, double *kernel_
 }
 
 // Task division over time: the stimulus is cut at T_k = k * slice_ps and the
-// slices are evaluated one after the other, each on the primary-input
-// transitions inside it, in slice-local time.  Every gate carries its state
-// across a boundary (input pin values, last output value, the scheduled
-// transitions at or past the boundary, which later inputs may still cancel
-// by Eq. 1); a transition scheduled before the boundary is final, because a
-// later input can only schedule at or after boundary + dmin.  So the slices'
-// outputs, concatenated, are the unsliced waveforms.  Each slice's waveforms
-// are copied to host memory; a slice whose arena overflows is evaluated again
-// with a larger one (its input state is still intact: double-buffered).
+// slices are evaluated in order, each on the primary-input transitions
+// inside it, in slice-local time.  Every gate carries its state across a
+// boundary (input pin values, last output value, the scheduled transitions
+// at or past the boundary, which later inputs may still cancel by Eq. 1); a
+// transition scheduled before the boundary is final, because a later input
+// can only schedule at or after boundary + dmin.  So the slices' outputs,
+// concatenated, are the unsliced waveforms.  Under the dependency schedule
+// one launch evaluates up to slice_group consecutive slices, a warp taking
+// its gate through all of them in turn once the gate's fanins are done for
+// all of them, so the per-gate costs are paid once per launch; under the
+// level schedule each slice is one set of level launches.  The waveforms of
+// a launch's slices are copied to host memory once it completes; a launch
+// whose arena overflows is evaluated again with a larger one (its input
+// state is never written by the launch).
 int run_sliced(gls_ctx *c, RunObj *r, cudaStream_t cs) {
     const RunItem &it = r->items[0];
     NetlistObj *n = find_netlist(c, it.netlist_id);
@@ -1331,16 +1355,24 @@ int run_sliced(gls_ctx *c, RunObj *r, cudaStream_t cs) {
     r->sliced_total = 0;
     r->sliced_demand = 0;
     r->sliced_ms = 0.0;
+    int in = 0;   // the state buffers holding the state at the next launch's start
     CK(cudaMemsetAsync(r->d_st[0], 0, sizeof(uint32_t) * (size_t)N, cs));   // start state
-    for (int32_t k = 0; k < ns; k++) {
-        const int64_t T0 = (int64_t)k * S, T1 = k == ns - 1 ? INT64_MAX : T0 + S;
+    for (int32_t k0 = 0; k0 < ns;) {
+        const int32_t L = std::min(r->slice_group, ns - k0);
+        const int o = (in + 1) % 3, a = (in + 2) % 3;
         RunDev d = r->dev;
-        d.st_in = r->d_st[k & 1];
-        d.st_out = r->d_st[(k + 1) & 1];
-        d.pend_in = r->d_pend[k & 1];
-        d.pend_out = r->d_pend[(k + 1) & 1];
-        d.slice_end = k == ns - 1 ? kTimeInf : (uint32_t)S;
-        d.slice_shift = k == 0 ? 0u : (uint32_t)S;
+        d.st_in = r->d_st[in];
+        d.st_out = r->d_st[o];
+        d.st_alt = r->d_st[a];
+        d.pend_in = r->d_pend[in];
+        d.pend_out = r->d_pend[o];
+        d.pend_alt = r->d_pend[a];
+        d.slices = L;
+        d.slice_nets = N;
+        d.slice_len = (uint32_t)S;
+        d.slice_end = k0 + L == ns ? kTimeInf : (uint32_t)S;   // of the launch's last slice
+        d.slice_shift = k0 == 0 ? 0u : (uint32_t)S;            // of its first
+        r->launch_slices = L;
         int64_t total = 0;
         double ms = 0.0;
         for (int attempt = 0;; attempt++) {
@@ -1350,15 +1382,15 @@ int run_sliced(gls_ctx *c, RunObj *r, cudaStream_t cs) {
             if (dep) CK(cudaMemsetAsync(d.done, 0, sizeof(uint32_t) * (size_t)N, cs));
             CK(cudaMemsetAsync(r->d_pi_total, 0, sizeof(unsigned long long), cs));
             CK(launch_slice_pack(s->d_off, s->wide ? nullptr : s->d_t, s->wide ? s->d_t64 : nullptr, s->d_v, n->n_pi,
-                                 T0, T1, r->d_slice_packed, d.net_ptr, d.net_len, dep ? d.done : nullptr,
-                                 r->d_pi_total, cs));
+                                 (int64_t)k0 * S, S, L, k0 + L == ns, N, r->d_slice_packed, d.net_ptr, d.net_len,
+                                 dep ? d.done : nullptr, r->d_pi_total, cs));
             CK(cudaEventRecord(r->ev0, cs));
             CK(launch_gates(c, r, d, cs));
             CK(cudaEventRecord(r->ev1, cs));
             const int rc = run_stats_impl(c, r, &total, &ms);
             if (rc == GLS_OK) break;
             if (rc != GLS_EOVERFLOW || attempt >= 8) return rc;
-            // total is a lower bound of this slice's demand: grow and evaluate it again
+            // total is a lower bound of this launch's demand: grow and evaluate it again
             const uint64_t want = std::max<uint64_t>(2 * r->dev.arena_cap, (uint64_t)total + total / 4 + (1u << 20));
             dfree(c, r->dev.arena);
             r->dev.arena = nullptr;
@@ -1374,17 +1406,21 @@ int run_sliced(gls_ctx *c, RunObj *r, cudaStream_t cs) {
         r->sliced_demand = std::max<int64_t>(r->sliced_demand, (int64_t)top);
         r->sliced_total += total;
         r->sliced_ms += ms;
-        RunObj::Slice sl;
-        sl.t0 = T0;
-        sl.off.assign((size_t)N + 1, 0);
-        int rc = read_item(c, r, 0, sl.off.data(), nullptr, 0);
-        if (rc != GLS_OK && rc != GLS_EOVERFLOW) return rc;
-        sl.packed.resize((size_t)sl.off[N]);
-        if (sl.off[N] > 0) {
-            rc = read_item(c, r, 0, sl.off.data(), sl.packed.data(), sl.off[N]);
-            if (rc) return rc;
+        for (int32_t j = 0; j < L; j++) {
+            RunObj::Slice sl;
+            sl.t0 = (int64_t)(k0 + j) * S;
+            sl.off.assign((size_t)N + 1, 0);
+            int rc = read_item(c, r, 0, sl.off.data(), nullptr, 0, (int64_t)j * N);
+            if (rc != GLS_OK && rc != GLS_EOVERFLOW) return rc;
+            sl.packed.resize((size_t)sl.off[N]);
+            if (sl.off[N] > 0) {
+                rc = read_item(c, r, 0, sl.off.data(), sl.packed.data(), sl.off[N], (int64_t)j * N);
+                if (rc) return rc;
+            }
+            r->slices.push_back(std::move(sl));
         }
-        r->slices.push_back(std::move(sl));
+        in = (L & 1) ? o : a;   // slice L - 1 wrote st_out when L - 1 is even, st_alt when odd
+        k0 += L;
     }
     return GLS_OK;
 }
@@ -1562,6 +1598,10 @@ int gls_set_option(gls_ctx *c, int option, int64_t value) {
     case GLS_OPT_SEGMENT:
         if (value < 1 || value > (1 << 20)) return fail(GLS_EINVAL, "segment target must be in [1, 2^20]");
         c->seg_target = (uint32_t)value;
+        return GLS_OK;
+    case GLS_OPT_SLICE_GROUP:
+        if (value < 1 || value > kMaxSliceGroup) return fail(GLS_EINVAL, "slice group must be in [1, %d]", kMaxSliceGroup);
+        c->slice_group = (int32_t)value;
         return GLS_OK;
     case GLS_OPT_HOST_MIRROR:
         if (value != 0 && value != 1) return fail(GLS_EINVAL, "host mirror must be 0 or 1");

@@ -1171,6 +1171,37 @@ __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin,
     }
 }
 
+// A gate over the consecutive time slices of a launch, one after the other:
+// each slice is evaluated as a gate of its own (its descriptor set, its state
+// buffers, its end and shift), and the state one slice leaves is where the
+// next one starts.  The gate's fanins are done for every slice of the launch
+// before it starts, so the per-gate costs (work claim, record, fanin waits,
+// publication) are paid once per launch instead of once per slice.
+template <int V, bool MIRROR>
+__device__ __forceinline__ bool eval_slices(const GateRec &gr, const RunDev &r, unsigned char *smem_raw, int warp,
+                                            int lane, uint32_t &par, WarpArena &wa) {
+    for (int j = 0; j < r.slices; j++) {
+        RunDev rj = r;
+        rj.net_ptr = r.net_ptr + (size_t)j * (size_t)r.slice_nets;
+        rj.net_len = r.net_len + (size_t)j * (size_t)r.slice_nets;
+        const bool odd = j & 1;
+        rj.st_in = j == 0 ? r.st_in : (odd ? r.st_out : r.st_alt);
+        rj.pend_in = j == 0 ? r.pend_in : (odd ? r.pend_out : r.pend_alt);
+        rj.st_out = odd ? r.st_alt : r.st_out;
+        rj.pend_out = odd ? r.pend_alt : r.pend_out;
+        rj.slice_end = j == r.slices - 1 ? r.slice_end : r.slice_len;
+        rj.slice_shift = j == 0 ? r.slice_shift : r.slice_len;
+        // the start state until this slice writes its own: a slice that does
+        // not (its arena overflowed, or its pending transitions did, and the
+        // launch is evaluated again or fails) hands the next one nothing to
+        // carry instead of an unwritten word
+        if (lane == 0) rj.st_out[gr.out_net] = 0u;
+        if (!eval_variant<V, true, MIRROR>(gr, rj, smem_raw, warp, lane, par, wa)) return false;
+        __syncwarp();   // this slice's state stores precede the next slice's loads
+    }
+    return true;
+}
+
 // Algorithm 1 without level barriers: gates are handed out in a topological
 // order (level order, or a planned critical-path-first order), so every fanin
 // gate of a handed-out gate was handed out earlier to a running warp and the
@@ -1178,8 +1209,9 @@ __global__ void level_kernel(const GateRec *__restrict__ gates, int32_t g_begin,
 // thread let 28 warps of the 128-transition windowed variant share an SM
 // (shared memory admits 7 CTAs of 4 warps).
 // Completion flags are per net: primary inputs start done, a gate's output
-// net is released once its waveform and descriptor are written.
-template <int V, bool MIRROR>
+// net is released once its waveform and descriptor are written (with MS, a
+// launch over several time slices: once all of its slices are).
+template <int V, bool MIRROR, bool MS>
 __global__ void __maxnreg__(V == kVariantWindowed ? 72 : GLS_WIDE_MAXNREG) dependency_kernel(const GateRec *__restrict__ gates, int32_t n_gates, int32_t ctr_slot, RunDev r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1215,11 +1247,22 @@ __global__ void __maxnreg__(V == kVariantWindowed ? 72 : GLS_WIDE_MAXNREG) depen
         if (ok) {
             // a window copy that never completed stops the warp (its readers
             // then give up their bounded waits)
-            if (!eval_variant<V, true, MIRROR>(gr, r, smem_raw, warp, lane, par, wa)) break;
+            if constexpr (MS) {
+                if (!eval_slices<V, MIRROR>(gr, r, smem_raw, warp, lane, par, wa)) break;
+            } else {
+                if (!eval_variant<V, true, MIRROR>(gr, r, smem_raw, warp, lane, par, wa)) break;
+            }
         } else if (lane == 0) {
             atomicOr(r.status, kStTimeout);
-            r.net_ptr[gr.out_net] = 0;
-            r.net_len[gr.out_net] = 0;
+            if constexpr (MS) {
+                for (int j = 0; j < r.slices; j++) {
+                    r.net_ptr[(size_t)j * (size_t)r.slice_nets + gr.out_net] = 0;
+                    r.net_len[(size_t)j * (size_t)r.slice_nets + gr.out_net] = 0;
+                }
+            } else {
+                r.net_ptr[gr.out_net] = 0;
+                r.net_len[gr.out_net] = 0;
+            }
         }
         // publish: this lane's output stores are ordered for the readers' bulk
         // copies (async proxy) and, through the warp barrier (which orders the
@@ -1242,19 +1285,25 @@ template <int V>
 static int max_ctas(int warps_per_cta) {
     const size_t sm = gate_smem_bytes(V, warps_per_cta);
     cudaFuncSetAttribute(level_kernel<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(dependency_kernel<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(dependency_kernel<V, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(level_kernel<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(dependency_kernel<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(dependency_kernel<V, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (sm > 0) {   // the windowed variants are limited by shared memory: prefer the largest carveout
         cudaFuncSetAttribute(level_kernel<V, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(dependency_kernel<V, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(dependency_kernel<V, false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         cudaFuncSetAttribute(level_kernel<V, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(dependency_kernel<V, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(dependency_kernel<V, true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }
-    int a = 0, b = 0;
+    int a = 0, b = 0, c = 1 << 30;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, level_kernel<V, false>, warps_per_cta * 32, sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dependency_kernel<V, false>, warps_per_cta * 32, sm);
-    return a < b ? a : b;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dependency_kernel<V, false, false>, warps_per_cta * 32, sm);
+    if constexpr (V != kVariantSegmented) {   // time slices per gate: the windowed variants only
+        cudaFuncSetAttribute(dependency_kernel<V, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(dependency_kernel<V, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, dependency_kernel<V, false, true>, warps_per_cta * 32, sm);
+    }
+    const int ab = a < b ? a : b;
+    return ab < c ? ab : c;
 }
 
 int gate_max_ctas_per_sm(int variant, int warps_per_cta) {
@@ -1285,14 +1334,18 @@ cudaError_t launch_dependency(const GateRec *d_gates, int32_t n_gates, int32_t c
     if (n_gates <= 0) return cudaSuccess;
     const int ctas = min(cfg.ctas, (n_gates + cfg.warps_per_cta - 1) / cfg.warps_per_cta);
     const size_t sm = gate_smem_bytes(cfg.variant, cfg.warps_per_cta);
+    const bool ms = r.slices > 1;   // several time slices per gate (windowed variants, no host mirror)
+    if (ms && (cfg.variant == kVariantSegmented || r.harena)) return cudaErrorInvalidValue;
     if (cfg.variant == kVariantSegmented)
-        dependency_kernel<kVariantSegmented, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+        dependency_kernel<kVariantSegmented, false, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
     else if (cfg.variant == kVariantWindowedWide) {
-        if (r.harena) dependency_kernel<kVariantWindowedWide, true><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
-        else dependency_kernel<kVariantWindowedWide, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+        if (ms) dependency_kernel<kVariantWindowedWide, false, true><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+        else if (r.harena) dependency_kernel<kVariantWindowedWide, true, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+        else dependency_kernel<kVariantWindowedWide, false, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
     } else {
-        if (r.harena) dependency_kernel<kVariantWindowed, true><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
-        else dependency_kernel<kVariantWindowed, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+        if (ms) dependency_kernel<kVariantWindowed, false, true><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+        else if (r.harena) dependency_kernel<kVariantWindowed, true, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
+        else dependency_kernel<kVariantWindowed, false, false><<<ctas, cfg.warps_per_cta * 32, sm, s>>>(d_gates, n_gates, ctr_slot, r);
     }
     return cudaGetLastError();
 }

@@ -88,6 +88,17 @@ struct RunDev {
                               // stored there too), or null
     uint32_t slice_end;       // local end of the slice: a t_r at or past it stays pending
     uint32_t slice_shift;     // start of this slice minus start of the previous one
+    // A dependency launch over `slices` > 1 consecutive time slices: a warp
+    // evaluates its gate over slice 0, 1, ... in turn.  Slice j's descriptors
+    // are net_ptr / net_len + j * slice_nets; slice 0 reads (st_in, pend_in)
+    // and writes (st_out, pend_out), slice j > 0 reads what slice j - 1
+    // wrote and writes the other buffer of the (out, alt) pair, so the
+    // launch's input state is never overwritten.  slice_end and slice_shift
+    // then hold the values of the launch's last and first slice.
+    int32_t slices;
+    uint32_t slice_len;       // slice length (local end of every slice but the run's last)
+    int64_t slice_nets;       // nets of one slice's descriptor set
+    uint32_t *st_alt, *pend_alt;
     unsigned long long *pi_total;   // primary-input transitions of the run (after time limits)
 };
 
@@ -123,6 +134,23 @@ __host__ __device__ inline uint64_t stim_words(int64_t n_events, int64_t n_pi) {
     return (uint64_t)(n_events + 3 * n_pi + 8);
 }
 
+// Most time slices one launch evaluates.
+constexpr int kMaxSliceGroup = 64;
+
+// Primary-input layout of a launch over L time slices: PI i's region starts
+// at word slice_base(off[i], i, L) = (off[i] + (4 L + 8) i + 3) & ~3, and the
+// slice-local transitions of its slice j, transitions lo..hi-1 of the PI
+// counted from its first transition in the launch's first slice, start at
+// region + ((lo + 4 j + 3) & ~3): 16-byte aligned, disjoint for consecutive
+// slices, and every read rounded up to 4 words stays inside the buffer of
+// slice_words(E, n_pi, L) words.
+__host__ __device__ inline uint64_t slice_base(int64_t off_i, int64_t i, int64_t L) {
+    return (uint64_t)((off_i + (4 * L + 8) * i + 3) & ~(int64_t)3);
+}
+__host__ __device__ inline uint64_t slice_words(int64_t n_events, int64_t n_pi, int64_t L) {
+    return (uint64_t)(n_events + (4 * L + 8) * n_pi + 8);
+}
+
 // ---- launch wrappers ----
 size_t gate_smem_bytes(int variant, int warps_per_cta);
 int gate_max_ctas_per_sm(int variant, int warps_per_cta);
@@ -134,13 +162,17 @@ cudaError_t launch_level(const GateRec *d_gates, int32_t g_begin, int32_t g_coun
 cudaError_t launch_dependency(const GateRec *d_gates, int32_t n_gates, int32_t ctr_slot, const RunDev &r,
                               const LevelCfg &cfg, cudaStream_t s);
 
-// Primary-input descriptors of one time slice [T0, T1): each PI's
-// transitions in the slice, as slice-local packed transitions at the start of
-// its 16-byte-aligned slot (stim_slot) of d_packed; done flags set; pi_total
-// accumulates the slice's PI transitions.  Exactly one of t32 / t64 is set.
+// Primary-input descriptors of L consecutive time slices [T0 + j S, T0 +
+// (j + 1) S), j < L (the last one open-ended if open_end): each PI's
+// transitions in slice j, as slice-local packed transitions at their aligned
+// place of d_packed (slice_base), described at net j * slice_nets + i; the
+// PIs' completion flags set (one per PI); pi_total accumulates the PI
+// transitions of the L slices.  Exactly one of t32 / t64 is set;
+// 1 <= L <= kMaxSliceGroup.
 cudaError_t launch_slice_pack(const int64_t *d_off, const int32_t *d_t32, const int64_t *d_t64, const uint8_t *d_v,
-                              int32_t n_pi, int64_t T0, int64_t T1, uint32_t *d_packed, uint64_t *net_ptr,
-                              uint32_t *net_len, uint32_t *done, unsigned long long *pi_total, cudaStream_t s);
+                              int32_t n_pi, int64_t T0, int64_t S, int32_t L, bool open_end, int64_t slice_nets,
+                              uint32_t *d_packed, uint64_t *net_ptr, uint32_t *net_len, uint32_t *done,
+                              unsigned long long *pi_total, cudaStream_t s);
 cudaError_t launch_pack_stimulus(const int64_t *d_off, const int32_t *d_t, const uint8_t *d_v, int32_t n_pi,
                                  uint32_t *d_packed, uint32_t *d_status, cudaStream_t s);
 cudaError_t launch_run_init(const int64_t *d_stim_off, const uint32_t *d_stim_packed, const RunDev &r,

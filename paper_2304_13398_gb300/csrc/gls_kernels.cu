@@ -50,34 +50,44 @@ __device__ __forceinline__ int64_t first_at_or_after(const TT *a, int64_t n, int
     return lo;
 }
 
-// One warp per primary input: the PI's transitions in the time slice
-// [T0, T1), moved to slice-local time (t - T0 fits 30 bits, checked on the
-// host) and packed at the start of the PI's aligned slot.
+// One warp per primary input: the PI's transitions in each of L consecutive
+// time slices, moved to slice-local time (t - slice start fits 30 bits,
+// checked on the host) and packed at their aligned place (slice_base).  The
+// L + 1 slice boundaries are found by binary searches, one per lane, and
+// kept in shared memory.
 template <typename TT>
-__global__ void slice_pack_kernel(const int64_t *__restrict__ off, const TT *__restrict__ t,
-                                  const uint8_t *__restrict__ v, int32_t n_pi, int64_t T0, int64_t T1,
-                                  uint32_t *__restrict__ packed, uint64_t *net_ptr, uint32_t *net_len, uint32_t *done,
-                                  unsigned long long *pi_total) {
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256) slice_pack_kernel(const int64_t *__restrict__ off, const TT *__restrict__ t,
+                                                         const uint8_t *__restrict__ v, int32_t n_pi, int64_t T0,
+                                                         int64_t S, int32_t L, bool open_end, int64_t slice_nets,
+                                                         uint32_t *__restrict__ packed, uint64_t *net_ptr,
+                                                         uint32_t *net_len, uint32_t *done,
+                                                         unsigned long long *pi_total) {
+    __shared__ int64_t bnd_all[8][kMaxSliceGroup + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t *bnd = bnd_all[w];
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     unsigned long long tot = 0;
-    for (int64_t pi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pi < n_pi; pi += warps) {
+    for (int64_t pi = (int64_t)blockIdx.x * (blockDim.x >> 5) + w; pi < n_pi; pi += warps) {
         const int64_t a = off[pi], n = off[pi + 1] - a;
-        int64_t lo = 0, hi = 0;
-        if (lane == 0) {
-            lo = first_at_or_after(t + a, n, T0);
-            hi = first_at_or_after(t + a, n, T1);
+        __syncwarp();   // the previous PI's reads of bnd are done
+        for (int j = lane; j <= L; j += 32)
+            bnd[j] = j == L && open_end ? n : first_at_or_after(t + a, n, T0 + (int64_t)j * S);
+        __syncwarp();
+        uint32_t *region = packed + slice_base(a, pi, L);
+        for (int j = 0; j < L; j++) {
+            const int64_t lo = bnd[j], hi = bnd[j + 1], tj = T0 + (int64_t)j * S;
+            uint32_t *dst = region + ((lo - bnd[0] + 4 * j + 3) & ~(int64_t)3);
+            for (int64_t e = lo + lane; e < hi; e += 32)
+                dst[e - lo] = ((uint32_t)((int64_t)t[a + e] - tj) << 2) | (v[a + e] & 3u);
+            if (lane == (j & 31)) {
+                const int64_t q = (int64_t)j * slice_nets + pi;
+                net_ptr[q] = reinterpret_cast<uint64_t>(dst);
+                net_len[q] = (uint32_t)(hi - lo);
+            }
         }
-        lo = __shfl_sync(FULL, lo, 0);
-        hi = __shfl_sync(FULL, hi, 0);
-        uint32_t *dst = packed + stim_slot(a, pi);
-        for (int64_t e = lo + lane; e < hi; e += 32)
-            dst[e - lo] = ((uint32_t)((int64_t)t[a + e] - T0) << 2) | (v[a + e] & 3u);
         if (lane == 0) {
-            net_ptr[pi] = reinterpret_cast<uint64_t>(dst);
-            net_len[pi] = (uint32_t)(hi - lo);
             if (done) done[pi] = 1u;
-            tot += (unsigned long long)(hi - lo);
+            tot += (unsigned long long)(bnd[L] - bnd[0]);
         }
     }
     if (lane == 0 && tot) atomicAdd(pi_total, tot);
@@ -240,15 +250,19 @@ cudaError_t launch_pack_stimulus(const int64_t *d_off, const int32_t *d_t, const
 }
 
 cudaError_t launch_slice_pack(const int64_t *d_off, const int32_t *d_t32, const int64_t *d_t64, const uint8_t *d_v,
-                              int32_t n_pi, int64_t T0, int64_t T1, uint32_t *d_packed, uint64_t *net_ptr,
-                              uint32_t *net_len, uint32_t *done, unsigned long long *pi_total, cudaStream_t s) {
+                              int32_t n_pi, int64_t T0, int64_t S, int32_t L, bool open_end, int64_t slice_nets,
+                              uint32_t *d_packed, uint64_t *net_ptr, uint32_t *net_len, uint32_t *done,
+                              unsigned long long *pi_total, cudaStream_t s) {
     if (n_pi <= 0) return cudaSuccess;
+    if (L < 1 || L > kMaxSliceGroup) return cudaErrorInvalidValue;
     if (d_t64)
-        slice_pack_kernel<int64_t><<<grid_for(n_pi, 8), 256, 0, s>>>(d_off, d_t64, d_v, n_pi, T0, T1, d_packed, net_ptr,
-                                                                     net_len, done, pi_total);
+        slice_pack_kernel<int64_t><<<grid_for(n_pi, 8), 256, 0, s>>>(d_off, d_t64, d_v, n_pi, T0, S, L, open_end,
+                                                                     slice_nets, d_packed, net_ptr, net_len, done,
+                                                                     pi_total);
     else
-        slice_pack_kernel<int32_t><<<grid_for(n_pi, 8), 256, 0, s>>>(d_off, d_t32, d_v, n_pi, T0, T1, d_packed, net_ptr,
-                                                                     net_len, done, pi_total);
+        slice_pack_kernel<int32_t><<<grid_for(n_pi, 8), 256, 0, s>>>(d_off, d_t32, d_v, n_pi, T0, S, L, open_end,
+                                                                     slice_nets, d_packed, net_ptr, net_len, done,
+                                                                     pi_total);
     return cudaGetLastError();
 }
 

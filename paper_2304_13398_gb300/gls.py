@@ -64,7 +64,7 @@ SIGNATURES = [
     ("gls_release", ctypes.c_int, [P, i32]),
 ]
 GLS_OPT_SCHEDULE, GLS_OPT_WARPS_PER_CTA, GLS_OPT_WAIT_LIMIT_MS, GLS_OPT_TEST_WITHHOLD_GATE, GLS_OPT_KERNEL, GLS_OPT_SEGMENT, \
-    GLS_OPT_POOL_BYTES, GLS_OPT_HOST_MIRROR, GLS_OPT_HOST_POOL_BYTES = 1, 2, 3, 4, 5, 6, 7, 8, 9
+    GLS_OPT_POOL_BYTES, GLS_OPT_HOST_MIRROR, GLS_OPT_HOST_POOL_BYTES, GLS_OPT_SLICE_GROUP = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10
 GLS_KERNEL_SEGMENTED, GLS_KERNEL_WINDOWED, GLS_KERNEL_WINDOWED_WIDE = 0, 1, 2
 KERNELS = {"segmented": GLS_KERNEL_SEGMENTED, "windowed": GLS_KERNEL_WINDOWED, "wide": GLS_KERNEL_WINDOWED_WIDE}
 GLS_SCHEDULE_LEVELS, GLS_SCHEDULE_DEPENDENCY = 0, 1
