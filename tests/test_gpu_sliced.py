@@ -168,3 +168,52 @@ def test_sliced_mid_size_industrial_shape():
         off, t, v = ctx.read_all64(rid)
         assert_same(ref, off, t, v, "20k gates, 1e6 ps slices")
         assert ctx.run_stats(rid).total_events == int(ref.off[-1] - ref.off[nl.n_pi])
+
+
+@pytest.mark.parametrize("group", [1, 2, 3, 5, 64])
+def test_slice_groups_equal_oracle(group):
+    """Launches of 1, 2, 3, 5 and up to 64 slices each: 700 ps slices of the
+    40,000 ps stimulus make 58 slices, so groups of 3 and 5 end with a
+    ragged launch, and odd and even group sizes hand the state buffers on
+    differently."""
+    nl, st = case(seed=101)
+    ref = oracle.sim_event(nl, st)
+    with gls.Context(0) as ctx:
+        ctx.set_option(gls.gls.GLS_OPT_SLICE_GROUP, group)
+        ctx.set_kernel("wide")
+        nid = ctx.load_netlist(nl)
+        sid = ctx.load_stimulus(st)
+        rid = ctx.simulate_sliced(nid, sid, 700)
+        assert ctx.run_slices(rid) == int(st.t.max()) // 700 + 1
+        off, t, v = ctx.read_all64(rid)
+        assert_same(ref, off, t, v, f"groups of {group}")
+        assert ctx.run_stats(rid).total_events == int(ref.off[-1] - ref.off[nl.n_pi])
+
+
+def test_slice_group_option_range():
+    with gls.Context(0) as ctx:
+        for bad in (0, 65, -1):
+            with pytest.raises(gls.GlsError):
+                ctx.set_option(gls.gls.GLS_OPT_SLICE_GROUP, bad)
+
+
+def test_sliced_bounded_wait_reports_timeout():
+    """A gate that never signals completion in a launch over several slices:
+    its readers give up after the wait limit, the call returns GLS_ETIMEOUT,
+    and the context stays usable."""
+    E = gls.gls
+    w = synth.make_workload("tiny200", seed=3)
+    nl, st = w.netlist, w.stimulus
+    with gls.Context(0) as c:
+        c.set_option(E.GLS_OPT_WAIT_LIMIT_MS, 50)
+        c.set_option(E.GLS_OPT_TEST_WITHHOLD_GATE, 0)   # first gate of level 1 has readers
+        nid = c.load_netlist(nl)
+        sid = c.load_stimulus(st)
+        with pytest.raises(gls.GlsError) as ei:
+            c.simulate_sliced(nid, sid, 20_000)
+        assert ei.value.code == E.GLS_ETIMEOUT
+        c.set_option(E.GLS_OPT_TEST_WITHHOLD_GATE, -1)
+        rid = c.simulate_sliced(nid, sid, 20_000)
+        assert c.run_slices(rid) > 1
+        off, t, v = c.read_all64(rid)
+        assert_same(oracle.sim_event(nl, st), off, t, v, "sliced after timeout")
