@@ -346,7 +346,8 @@ struct RunObj {
     struct Slice {
         int64_t t0;                     // start of the slice (local time 0)
         std::vector<int64_t> off;       // [n_nets + 1] caller net order
-        std::vector<uint32_t> packed;   // slice-local (t << 2) | v
+        std::unique_ptr<uint32_t[]> packed;   // slice-local (t << 2) | v, off[n_nets] words (not
+                                              // zero-filled: the copy from the device writes all of it)
     };
     std::vector<Slice> slices;
     int64_t sliced_total = 0, sliced_demand = 0;
@@ -1412,9 +1413,9 @@ int run_sliced(gls_ctx *c, RunObj *r, cudaStream_t cs) {
             sl.off.assign((size_t)N + 1, 0);
             int rc = read_item(c, r, 0, sl.off.data(), nullptr, 0, (int64_t)j * N);
             if (rc != GLS_OK && rc != GLS_EOVERFLOW) return rc;
-            sl.packed.resize((size_t)sl.off[N]);
             if (sl.off[N] > 0) {
-                rc = read_item(c, r, 0, sl.off.data(), sl.packed.data(), sl.off[N], (int64_t)j * N);
+                sl.packed.reset(new uint32_t[(size_t)sl.off[N]]);
+                rc = read_item(c, r, 0, sl.off.data(), sl.packed.get(), sl.off[N], (int64_t)j * N);
                 if (rc) return rc;
             }
             r->slices.push_back(std::move(sl));
