@@ -426,8 +426,10 @@ typedef enum gls_option {
                                    size now and carve the host mirrors of later runs
                                    (GLS_OPT_HOST_MIRROR) from it, first fit, instead of pinning
                                    new host memory per run; GLS_ENOMEM at run creation when no
-                                   block is large enough.  0: free it.  Only when no mirror is
-                                   in use. */
+                                   block is large enough.  Sliced runs also keep their slices'
+                                   waveforms in it while it has room (the copies from the
+                                   device then run at the link's rate), else in ordinary host
+                                   memory.  0: free it.  Only when no block is in use. */
     GLS_OPT_SLICE_GROUP = 10    /* sliced runs under the dependency schedule: most time slices
                                    one launch evaluates, 1..64 (default 64) */
 } gls_option;

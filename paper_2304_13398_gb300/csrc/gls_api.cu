@@ -346,8 +346,13 @@ struct RunObj {
     struct Slice {
         int64_t t0;                     // start of the slice (local time 0)
         std::vector<int64_t> off;       // [n_nets + 1] caller net order
-        std::unique_ptr<uint32_t[]> packed;   // slice-local (t << 2) | v, off[n_nets] words (not
-                                              // zero-filled: the copy from the device writes all of it)
+        // slice-local (t << 2) | v, off[n_nets] words: carved from the
+        // pinned host pool when the context has one (the copies from the
+        // device then run at the link's rate), else ordinary host memory
+        // that is not zero-filled first (the copy writes all of it)
+        std::unique_ptr<uint32_t[]> heap;
+        uint32_t *pinned = nullptr;
+        const uint32_t *words() const { return pinned ? pinned : heap.get(); }
     };
     std::vector<Slice> slices;
     int64_t sliced_total = 0, sliced_demand = 0;
@@ -507,6 +512,13 @@ void free_stim(gls_ctx *c, StimObj *s) {
     dfree(c, s->d_packed);
     dfree(c, s->d_t64);
 }
+// The host copies of a sliced run's slices (pool blocks back to the pinned pool).
+void release_slices(gls_ctx *c, RunObj *r) {
+    for (auto &sl : r->slices)
+        if (sl.pinned) pool_give(c->hpool, sl.pinned);
+    r->slices.clear();
+}
+
 void free_run(gls_ctx *c, RunObj *r) {
     if (r->exec) cudaGraphExecDestroy(r->exec);
     if (r->ev0) cudaEventDestroy(r->ev0);
@@ -527,6 +539,7 @@ void free_run(gls_ctx *c, RunObj *r) {
     dfree(c, r->d_slice_packed);
     dfree(c, r->d_glen);
     if (r->h_arena && !pool_give(c->hpool, r->h_arena)) cudaFreeHost(r->h_arena);
+    release_slices(c, r);
     for (int k = 0; k < 3; k++) {
         dfree(c, r->d_st[k]);
         dfree(c, r->d_pend[k]);
@@ -1352,7 +1365,7 @@ int run_sliced(gls_ctx *c, RunObj *r, cudaStream_t cs) {
     const int64_t mt = s->wide ? s->max_time64 : (int64_t)s->max_time;
     const int32_t ns = s->n_events > 0 ? (int32_t)(mt / S + 1) : 1;
     const bool dep = r->schedule == GLS_SCHEDULE_DEPENDENCY;
-    r->slices.clear();
+    release_slices(c, r);
     r->sliced_total = 0;
     r->sliced_demand = 0;
     r->sliced_ms = 0.0;
@@ -1413,12 +1426,19 @@ int run_sliced(gls_ctx *c, RunObj *r, cudaStream_t cs) {
             sl.off.assign((size_t)N + 1, 0);
             int rc = read_item(c, r, 0, sl.off.data(), nullptr, 0, (int64_t)j * N);
             if (rc != GLS_OK && rc != GLS_EOVERFLOW) return rc;
-            if (sl.off[N] > 0) {
-                sl.packed.reset(new uint32_t[(size_t)sl.off[N]]);
-                rc = read_item(c, r, 0, sl.off.data(), sl.packed.get(), sl.off[N], (int64_t)j * N);
+            uint32_t *dst = nullptr;
+            const int64_t n_words = sl.off[N];
+            if (n_words > 0) {
+                if (c->hpool.base)
+                    dst = static_cast<uint32_t *>(pool_take(c->hpool, sizeof(uint32_t) * (uint64_t)n_words, false));
+                if (dst) sl.pinned = dst;
+                else sl.heap.reset(dst = new uint32_t[(size_t)n_words]);
+            }
+            r->slices.push_back(std::move(sl));   // the run owns the storage (and its pool block) from here
+            if (dst) {
+                rc = read_item(c, r, 0, r->slices.back().off.data(), dst, n_words, (int64_t)j * N);
                 if (rc) return rc;
             }
-            r->slices.push_back(std::move(sl));
         }
         in = (L & 1) ? o : a;   // slice L - 1 wrote st_out when L - 1 is even, st_alt when odd
         k0 += L;
@@ -1635,7 +1655,8 @@ int gls_set_option(gls_ctx *c, int option, int64_t value) {
     case GLS_OPT_HOST_POOL_BYTES: {
         if (value < 0) return fail(GLS_EINVAL, "host pool size must be >= 0");
         if (!c->hpool.allocs.empty())
-            return fail(GLS_EINVAL, "the host pool still holds %zu mirrors", c->hpool.allocs.size());
+            return fail(GLS_EINVAL, "the host pool still holds %zu blocks (run mirrors or sliced results)",
+                        c->hpool.allocs.size());
         if (c->hpool.base) {
             CK(cudaFreeHost(c->hpool.base));
             c->hpool = Pool{};
@@ -1823,11 +1844,13 @@ int gls_read_all64(gls_ctx *c, int32_t run_id, int64_t *off, int64_t *t, uint8_t
     if (off[N] > 0 && (!t || !v)) return fail(GLS_EINVAL, "NULL output arrays");
     for (int64_t q = 0; q < N; q++) {
         int64_t o = off[q];
-        for (const auto &sl : r->slices)
+        for (const auto &sl : r->slices) {
+            const uint32_t *w = sl.words();
             for (int64_t e = sl.off[q]; e < sl.off[q + 1]; e++, o++) {
-                t[o] = sl.t0 + (int64_t)(sl.packed[e] >> 2);
-                v[o] = (uint8_t)(sl.packed[e] & 3u);
+                t[o] = sl.t0 + (int64_t)(w[e] >> 2);
+                v[o] = (uint8_t)(w[e] & 3u);
             }
+        }
     }
     return GLS_OK;
 }
@@ -1845,11 +1868,13 @@ int gls_read_waveform64(gls_ctx *c, int32_t run_id, int32_t net, int64_t *t, uin
     if (len > cap) return fail(GLS_EOVERFLOW, "%lld transitions, cap %lld", (long long)len, (long long)cap);
     if (len > 0 && (!t || !v)) return fail(GLS_EINVAL, "NULL output arrays");
     int64_t o = 0;
-    for (const auto &sl : r->slices)
+    for (const auto &sl : r->slices) {
+        const uint32_t *w = sl.words();
         for (int64_t e = sl.off[net]; e < sl.off[net + 1]; e++, o++) {
-            t[o] = sl.t0 + (int64_t)(sl.packed[e] >> 2);
-            v[o] = (uint8_t)(sl.packed[e] & 3u);
+            t[o] = sl.t0 + (int64_t)(w[e] >> 2);
+            v[o] = (uint8_t)(w[e] & 3u);
         }
+    }
     return GLS_OK;
 }
 

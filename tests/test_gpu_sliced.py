@@ -217,3 +217,30 @@ def test_sliced_bounded_wait_reports_timeout():
         assert c.run_slices(rid) > 1
         off, t, v = c.read_all64(rid)
         assert_same(oracle.sim_event(nl, st), off, t, v, "sliced after timeout")
+
+
+def test_sliced_results_in_the_pinned_host_pool():
+    """With a pinned host pool the slices' waveforms are carved from it; the
+    pool cannot be dropped while the run holds blocks, and can once the run
+    is released.  A pool too small for a slice falls back to ordinary host
+    memory."""
+    nl, st = case(seed=121)
+    ref = oracle.sim_event(nl, st)
+    E = gls.gls
+    with gls.Context(0) as ctx:
+        ctx.set_kernel("wide")
+        nid = ctx.load_netlist(nl)
+        sid = ctx.load_stimulus(st)
+        for pool in (64 << 20, 4096):
+            ctx.set_option(E.GLS_OPT_HOST_POOL_BYTES, pool)
+            rid = ctx.simulate_sliced(nid, sid, 3_000)
+            off, t, v = ctx.read_all64(rid)
+            assert_same(ref, off, t, v, f"host pool of {pool} bytes")
+            ctx.rerun(rid)                      # the slices' blocks are given back and taken again
+            off, t, v = ctx.read_all64(rid)
+            assert_same(ref, off, t, v, f"host pool of {pool} bytes, rerun")
+            if pool > 4096:
+                with pytest.raises(gls.GlsError):
+                    ctx.set_option(E.GLS_OPT_HOST_POOL_BYTES, 0)   # blocks in use
+            ctx.release(rid)
+            ctx.set_option(E.GLS_OPT_HOST_POOL_BYTES, 0)
