@@ -707,9 +707,13 @@ def run_sliced(a):
         rid = ctx.simulate_sliced(nid, stim_id, slice_ps)
         wall = time.perf_counter() - t0
         stt = ctx.run_stats(rid)
+        t0 = time.perf_counter()
+        off64, t64, v64 = ctx.read_all64(rid)   # every waveform, 64-bit times, in caller net order
+        read_s = time.perf_counter() - t0
+        del off64, t64, v64
         out[label] = {"slice_ps": slice_ps, "slices": ctx.run_slices(rid), "transitions": stt.total_events,
                       "device_ms": stt.kernel_ms, "value": stt.total_events / (stt.kernel_ms / 1000.0),
-                      "wall_s": wall, "wall_value": stt.total_events / wall,
+                      "wall_s": wall, "wall_value": stt.total_events / wall, "read_all64_s": read_s,
                       "equal_transitions_to_unsliced": stt.total_events == plain.total_events}
         ctx.release(rid)
     ctx.release(sid)

@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -1842,16 +1843,36 @@ int gls_read_all64(gls_ctx *c, int32_t run_id, int64_t *off, int64_t *t, uint8_t
     }
     if (off[N] > cap) return fail(GLS_EOVERFLOW, "%lld transitions, cap %lld", (long long)off[N], (long long)cap);
     if (off[N] > 0 && (!t || !v)) return fail(GLS_EINVAL, "NULL output arrays");
-    for (int64_t q = 0; q < N; q++) {
-        int64_t o = off[q];
-        for (const auto &sl : r->slices) {
-            const uint32_t *w = sl.words();
-            for (int64_t e = sl.off[q]; e < sl.off[q + 1]; e++, o++) {
-                t[o] = sl.t0 + (int64_t)(w[e] >> 2);
-                v[o] = (uint8_t)(w[e] & 3u);
+    // widen every slice's words into the caller's arrays, nets split over the
+    // host's cores when there is enough to do (each net's range is its own)
+    auto widen = [&](int64_t q0, int64_t q1) {
+        for (int64_t q = q0; q < q1; q++) {
+            int64_t o = off[q];
+            for (const auto &sl : r->slices) {
+                const uint32_t *w = sl.words();
+                for (int64_t e = sl.off[q]; e < sl.off[q + 1]; e++, o++) {
+                    t[o] = sl.t0 + (int64_t)(w[e] >> 2);
+                    v[o] = (uint8_t)(w[e] & 3u);
+                }
             }
         }
+    };
+    const int64_t nt = off[N] < (1 << 22) ? 1 : std::min<int64_t>(16, std::max(1u, std::thread::hardware_concurrency()));
+    if (nt == 1) {
+        widen(0, N);
+        return GLS_OK;
     }
+    std::vector<std::thread> pool;
+    int64_t done_to = 0;   // nets widened by this thread when a worker cannot be started
+    try {
+        for (int64_t k = 0; k < nt; k++) {
+            pool.emplace_back(widen, N * k / nt, N * (k + 1) / nt);
+            done_to = N * (k + 1) / nt;
+        }
+    } catch (const std::exception &) {
+        widen(done_to, N);
+    }
+    for (auto &th : pool) th.join();
     return GLS_OK;
 }
 
