@@ -378,7 +378,9 @@ int gls_run_slices(gls_ctx *ctx, int32_t run_id, int32_t *n_slices);
 
 /* Every net's waveform of a sliced run, in net id order: off[n_nets + 1]
    (always filled), 64-bit times t[cap] and values v[cap].  GLS_EOVERFLOW if
-   cap is below the total.  Host memory only. */
+   cap is below the total.  Host memory only; results of more than 4 Mi
+   transitions are widened on up to 16 host threads (Sec. 3.1 storage read
+   back as one CSR over the whole stimulus). */
 int gls_read_all64(gls_ctx *ctx, int32_t run_id, int64_t *off, int64_t *t, uint8_t *v, int64_t cap);
 
 /* One net's waveform of a sliced run: *n_out always receives its length;
