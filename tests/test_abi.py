@@ -36,6 +36,23 @@ def test_exports_every_declared_symbol(lib):
     assert set(names) == bound, "binding and header disagree"
 
 
+def declared_constants():
+    """Every GLS_* enumerator of the header with its value."""
+    src = open(os.path.join(ROOT, "include", "gls.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(GLS_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+
+
+def test_binding_constants_equal_header():
+    consts = declared_constants()
+    assert "GLS_OPT_SLICE_GROUP" in consts and "GLS_ETIMEOUT" in consts
+    for name, value in consts.items():
+        if hasattr(gls.gls, name):
+            assert getattr(gls.gls, name) == value, name
+    for name in [n for n in consts if n.startswith(("GLS_OPT_", "GLS_KERNEL_", "GLS_SCHEDULE_"))]:
+        assert hasattr(gls.gls, name), f"{name} is not in the binding"
+
+
 def test_version_and_arity(lib):
     assert lib.gls_version() >= 100
     assert [lib.gls_cell_arity(c) for c in range(11)] == [1, 1, 2, 2, 2, 2, 2, 2, 3, 3, 3]
