@@ -677,8 +677,9 @@ def run_sliced(a):
     import paper_2304_13398_gb300 as gls
     import synth
     torch.cuda.set_device(0)
-    w = synth.make_workload(a.workload, seed=a.seed)
+    w = synth.make_workload(a.workload, seed=a.seed, **overrides(a))
     nl, st = w.netlist, w.stimulus
+    arena = int(a.arena_words)   # 0: the library's default (profiling cases set it)
     ctx = gls.Context(0)
     ctx.set_kernel(a.kernel)
     host_pool = int(min(0.45 * mem_available_bytes(), 16 << 30))
@@ -686,9 +687,8 @@ def run_sliced(a):
     nid = ctx.load_netlist(nl)
     order = plan_from_calibration(ctx, nid, nl, w.recipe["stim"], a.seed)
     sid = ctx.load_stimulus(st)
-    rid = ctx.simulate(nid, sid)
+    rid = ctx.simulate(nid, sid, arena_events=arena)
     rc, demand, _ = ctx.run_stats_raw(rid)
-    arena = 0
     while rc == gls.gls.GLS_EOVERFLOW:
         ctx.release(rid)
         arena = int(demand * 1.25) + 1024
@@ -701,10 +701,10 @@ def run_sliced(a):
     ctx.release(rid)
     out = {}
     for label, stim_id, slice_ps in [("sliced_1m", sid, a.slice_ps)]:
-        rid = ctx.simulate_sliced(nid, stim_id, slice_ps)
+        rid = ctx.simulate_sliced(nid, stim_id, slice_ps, arena_events=arena)
         ctx.release(rid)
         t0 = time.perf_counter()
-        rid = ctx.simulate_sliced(nid, stim_id, slice_ps)
+        rid = ctx.simulate_sliced(nid, stim_id, slice_ps, arena_events=arena)
         wall = time.perf_counter() - t0
         stt = ctx.run_stats(rid)
         t0 = time.perf_counter()
@@ -717,26 +717,27 @@ def run_sliced(a):
                       "equal_transitions_to_unsliced": stt.total_events == plain.total_events}
         ctx.release(rid)
     ctx.release(sid)
-    sp = dict(w.recipe["stim"])
-    sp["window"] = int(a.long_window)
-    lst = synth.make_stimulus(nl.n_pi, seed=a.seed + 1000003, **sp)   # 64-bit times past 2^31 ps
-    lid = ctx.load_stimulus64(lst)
-    rid = ctx.simulate_sliced(nid, lid, 1 << 29)
-    stt = ctx.run_stats(rid)
-    ctx.release(rid)
-    t0 = time.perf_counter()
-    rid = ctx.simulate_sliced(nid, lid, 1 << 29)
-    wall = time.perf_counter() - t0
-    stt = ctx.run_stats(rid)
-    out["long_64bit"] = {"window_ps": int(a.long_window), "slice_ps": 1 << 29, "slices": ctx.run_slices(rid),
-                         "stimulus_transitions": int(lst.n_events), "transitions": stt.total_events,
-                         "device_ms": stt.kernel_ms, "value": stt.total_events / (stt.kernel_ms / 1000.0),
-                         "wall_s": wall, "wall_value": stt.total_events / wall}
-    ctx.release(rid)
+    if a.long_window > 0:   # 0: the workload in slices only (profiling cases)
+        sp = dict(w.recipe["stim"])
+        sp["window"] = int(a.long_window)
+        lst = synth.make_stimulus(nl.n_pi, seed=a.seed + 1000003, **sp)   # 64-bit times past 2^31 ps
+        lid = ctx.load_stimulus64(lst)
+        rid = ctx.simulate_sliced(nid, lid, 1 << 29)
+        stt = ctx.run_stats(rid)
+        ctx.release(rid)
+        t0 = time.perf_counter()
+        rid = ctx.simulate_sliced(nid, lid, 1 << 29)
+        wall = time.perf_counter() - t0
+        stt = ctx.run_stats(rid)
+        out["long_64bit"] = {"window_ps": int(a.long_window), "slice_ps": 1 << 29, "slices": ctx.run_slices(rid),
+                             "stimulus_transitions": int(lst.n_events), "transitions": stt.total_events,
+                             "device_ms": stt.kernel_ms, "value": stt.total_events / (stt.kernel_ms / 1000.0),
+                             "wall_s": wall, "wall_value": stt.total_events / wall}
+        ctx.release(rid)
     ctx.close()
     line = {"metric": "sliced output transitions/s (task division over time, 1M gates)", "unit": UNIT,
             "mode": "sliced", "n_gpus": 1, "higher_is_better": True, "kernel": a.kernel, "gate_order": order,
-            "host_pool_bytes": host_pool,
+            "host_pool_bytes": host_pool, "config": describe(a.workload, w),
             "unsliced": {"transitions": plain.total_events, "device_ms": plain.kernel_ms,
                          "value": plain.total_events / (plain.kernel_ms / 1000.0)},
             **out, "data": "synthetic", "dtype": "u32"}
