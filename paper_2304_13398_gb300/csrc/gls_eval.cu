@@ -360,174 +360,16 @@ __device__ __forceinline__ bool commit_chunk(WarpSmem<CH> &sm, int lane, int d0,
     return true;
 }
 
-// Returns false only when a window copy did not complete within its poll
-// bound (the warp then stops: its buffers may still be written).
-template <int K, bool DEP, int CH, bool EDGE, bool MIRROR>
-__device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane, uint32_t &par,
-                          WarpArena &wa) {
-    GateCtx g;
-    uint64_t bound = 0;
-#pragma unroll
-    for (int p = 0; p < 3; p++) {
-        if (p < K) {
-            const int32_t n = gr.fin[p];
-            uint64_t ptr;
-            uint32_t len;
-            if (DEP) {  // written during this launch: read through L2
-                ptr = __ldcg(reinterpret_cast<const unsigned long long *>(r.net_ptr) + n);
-                len = __ldcg(r.net_len + n);
-            } else {
-                ptr = __ldg(reinterpret_cast<const unsigned long long *>(r.net_ptr) + n);
-                len = __ldg(r.net_len + n);
-            }
-            g.src[p] = reinterpret_cast<const uint32_t *>(ptr);
-            g.len[p] = len;
-        } else {
-            g.src[p] = nullptr;
-            g.len[p] = 0;
-        }
-        bound += g.len[p];
-    }
-    const uint32_t out_net = gr.out_net;
-
-    // state before the first input transition: pins at X, output X, nothing
-    // pending -- or, in a time slice, where the previous slice left the gate
-    uint32_t carry = 0x2Au;
-    CommitState cs{0u, kVX, 0};
-    uint32_t send = kTimeInf;   // transitions with t_r >= send stay pending
-    bool started = false;       // an input transition was evaluated (else the output is still at its X start)
-    if (r.st_in) {
-        const uint32_t h = r.st_in[out_net];
-        carry = (h & 63u) ^ 0x2Au;
-        started = (h >> 7) & 1u;
-        cs.lastV = ((h >> 8) & 3u) ^ kVX;
-        cs.np = (int)(h >> 16);
-        bound += (uint64_t)cs.np;   // each carried transition may become an output
-        send = r.slice_end;
-    }
-    if (bound == 0) {   // no input transition: the output stays as it is (X at the start, Algorithm 2)
-        if (lane == 0) {
-            r.net_ptr[out_net] = 0;
-            r.net_len[out_net] = 0;
-            if (r.st_in) r.st_out[out_net] = r.st_in[out_net];
-        }
-        return true;
-    }
-
-    // Claim the output slot and start the first window copies before the
-    // per-gate tables are built, so that the atomic's and the copies'
-    // latencies overlap that work.
-    const uint64_t need = (bound + kSlotAlign - 1) & ~(uint64_t)(kSlotAlign - 1);
-    const bool claim = wa.cur + need > wa.end;   // the same on every lane
-    const uint64_t blk = need > r.arena_blk ? need : (uint64_t)r.arena_blk;
-    unsigned long long base = 0;
-    if (claim && lane == 0) base = atomicAdd(r.arena_top, (unsigned long long)blk);
-    uint32_t cur[3] = {0, 0, 0};
-    bool failed = false;
+// Steps 1-5 for every chunk of one gate's inputs (or of one time slice's):
+// the chunk cut, the merge and per-lane walk, the window refill and the
+// commit, until the windows are exhausted.  Returns false only when a window
+// copy did not complete within its poll bound.
+template <int K, int CH, bool EDGE, bool MIRROR>
+__device__ __forceinline__ bool run_chunks(const RunDev &r, WarpSmem<CH> &sm, GateCtx &g, int lane, uint32_t &par,
+                                           bool &more, uint32_t (&cur)[3], int (&lead)[3], int (&n)[3],
+                                           uint32_t &carry, bool &started, CommitState &cs, uint32_t send,
+                                           uint32_t *out, uint32_t *hout, bool &failed) {
     const int b = 0;   // the one window buffer
-    int lead[3] = {0, 0, 0}, n[3] = {0, 0, 0};
-    __syncwarp();      // the previous gate's reads of the buffer precede the copies
-    bool more = issue_windows<K, CH>(sm, 0, g, cur, lead, n, lane);
-    const bool any_input = more;
-
-    g.dmin = (uint32_t)gr.dmin;
-    g.lut_lo = gr.lut_lo;
-    g.lut_hi = gr.lut_hi;
-    // delay tables from the record's [pin][edge][value] offsets
-    const uint32_t arcs = gr.arcs;
-    uint32_t fb_f = 255u, fb_r = 255u, omax = 0;   // fastest arcs to 0 / to 1, slowest arc
-#pragma unroll
-    for (int p = 0; p < K; p++)
-        if ((arcs >> p) & 1u)
-#pragma unroll
-            for (int e = 0; e < 2; e++) {
-                fb_f = min(fb_f, (uint32_t)gr.doff[p][e][0]);
-                fb_r = min(fb_r, (uint32_t)gr.doff[p][e][1]);
-                omax = max(omax, max((uint32_t)gr.doff[p][e][0], (uint32_t)gr.doff[p][e][1]));
-            }
-    g.dmax = g.dmin + omax;
-    g.rise[0] = g.dmin + gr.doff[0][0][1];
-    g.fall[0] = g.dmin + gr.doff[0][0][0];
-    g.dx[0] = min(g.rise[0], g.fall[0]);
-    g.df_lo = g.df_hi = g.dr_lo = g.dr_hi = 0;
-    if (!EDGE) {
-#pragma unroll
-        for (int set = 1; set < 8; set++) {
-            uint32_t f = 255u, rr = 255u;   // sets with a pin >= K never occur
-            const uint32_t in = (uint32_t)set & arcs;
-#pragma unroll
-            for (int p = 0; p < K; p++)
-                if ((in >> p) & 1u) { f = min(f, (uint32_t)gr.doff[p][0][0]); rr = min(rr, (uint32_t)gr.doff[p][0][1]); }
-            if (in == 0) { f = fb_f; rr = fb_r; }
-            if (set < 4) { g.df_lo |= f << (8 * set); g.dr_lo |= rr << (8 * set); }
-            else { g.df_hi |= f << (8 * (set - 4)); g.dr_hi |= rr << (8 * (set - 4)); }
-        }
-        g.dx_lo = __vminu4(g.df_lo, g.dr_lo);
-        g.dx_hi = __vminu4(g.df_hi, g.dr_hi);
-        if (K == 3) {   // delay - dmin by new value and changed-pin set; value by pin values
-            for (int x = lane; x < 24; x += 32) {
-                const uint32_t F = (uint32_t)x >> 3, grp = (uint32_t)x & 7u;
-                sm.dtab[F][grp] = (uint8_t)(group_delay<3>(g, F, grp) - g.dmin);
-            }
-            for (int x = lane; x < 64; x += 32)
-                sm.f3[x] = (uint8_t)((((x & 32) ? g.lut_hi : g.lut_lo) >> (2 * (x & 31))) & 3u);
-            __syncwarp();
-        }
-        if (K == 2) {
-            const uint32_t l2 = (uint32_t)g.lut_hi;
-            for (int x = lane; x < 64; x += 32) {
-                const uint32_t F = (l2 >> (2 * (x & 15))) & 3u, grp = (uint32_t)x >> 4;
-                sm.ftab[x] = (uint16_t)(((group_delay<2>(g, F, grp) - g.dmin) << 2) | F);
-            }
-            __syncwarp();
-        }
-    } else {
-        for (int x = lane; x < 192; x += 32) {
-            const int F = x >> 6, vm = x & 63;
-            uint32_t d = 255u;
-            bool any = false;
-#pragma unroll
-            for (int p = 0; p < K; p++)
-#pragma unroll
-                for (int e = 0; e < 2; e++)
-                    if (((vm >> (2 * p + e)) & 1) && ((arcs >> p) & 1u)) {
-                        const uint32_t d0 = gr.doff[p][e][0], d1 = gr.doff[p][e][1];
-                        d = min(d, F == 0 ? d0 : (F == 1 ? d1 : min(d0, d1)));
-                        any = true;
-                    }
-            if (!any) d = F == 0 ? fb_f : (F == 1 ? fb_r : min(fb_f, fb_r));
-            sm.dtab[F][vm] = (uint8_t)d;
-        }
-        __syncwarp();
-    }
-    if (claim) {
-        base = __shfl_sync(FULL, base, 0);
-        wa.end = base + blk;
-    } else {
-        base = wa.cur;
-    }
-    if (base + bound > r.arena_cap) {
-        wa.cur = wa.end = 0;   // past the arena: the next gate claims again (and counts its demand)
-        if (lane == 0) {
-            atomicOr(r.status, kStArenaOverflow);
-            r.net_ptr[out_net] = 0;
-            r.net_len[out_net] = 0;
-        }
-        // the copies already issued land in this warp's buffer: let them finish
-        if (more && !wait_window(sm, b, par)) {
-            if (lane == 0) atomicOr(r.status, kStTimeout);
-            return false;
-        }
-        return true;
-    }
-    uint32_t *out = r.arena + base;
-    uint32_t *hout = MIRROR ? r.harena + base : nullptr;
-    if (cs.np > 0) {   // carried transitions, moved to this slice's local time
-        const uint32_t *pp = r.pend_in + (size_t)out_net * PCAP;
-        for (int x = lane; x < cs.np; x += 32) sm.Q[x] = pp[x] - (r.slice_shift << 2);
-        __syncwarp();
-    }
-
     // 4-value tables: K == 1 uses f(a) with b = c = X (entries 40..43),
     // K == 2 uses f(a, b) with c = X (entries 32..47), K == 3 all 64
     const uint32_t lut1 = (uint32_t)(g.lut_hi >> 16) & 0xFFu;
@@ -756,6 +598,188 @@ __device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, 
         if (lane == 0) atomicOr(r.status, kStTimeout);
         return false;
     }
+    return true;
+}
+
+// A gate's delay and value tables from its record: the register part
+// (GateCtx) and the shared-memory tables of two- and three-input cells and
+// of edge-dependent delays.
+template <int K, int CH, bool EDGE>
+__device__ __forceinline__ void build_tables(const GateRec &gr, GateCtx &g, WarpSmem<CH> &sm, int lane) {
+    g.dmin = (uint32_t)gr.dmin;
+    g.lut_lo = gr.lut_lo;
+    g.lut_hi = gr.lut_hi;
+    // delay tables from the record's [pin][edge][value] offsets
+    const uint32_t arcs = gr.arcs;
+    uint32_t fb_f = 255u, fb_r = 255u, omax = 0;   // fastest arcs to 0 / to 1, slowest arc
+#pragma unroll
+    for (int p = 0; p < K; p++)
+        if ((arcs >> p) & 1u)
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                fb_f = min(fb_f, (uint32_t)gr.doff[p][e][0]);
+                fb_r = min(fb_r, (uint32_t)gr.doff[p][e][1]);
+                omax = max(omax, max((uint32_t)gr.doff[p][e][0], (uint32_t)gr.doff[p][e][1]));
+            }
+    g.dmax = g.dmin + omax;
+    g.rise[0] = g.dmin + gr.doff[0][0][1];
+    g.fall[0] = g.dmin + gr.doff[0][0][0];
+    g.dx[0] = min(g.rise[0], g.fall[0]);
+    g.df_lo = g.df_hi = g.dr_lo = g.dr_hi = 0;
+    if (!EDGE) {
+#pragma unroll
+        for (int set = 1; set < 8; set++) {
+            uint32_t f = 255u, rr = 255u;   // sets with a pin >= K never occur
+            const uint32_t in = (uint32_t)set & arcs;
+#pragma unroll
+            for (int p = 0; p < K; p++)
+                if ((in >> p) & 1u) { f = min(f, (uint32_t)gr.doff[p][0][0]); rr = min(rr, (uint32_t)gr.doff[p][0][1]); }
+            if (in == 0) { f = fb_f; rr = fb_r; }
+            if (set < 4) { g.df_lo |= f << (8 * set); g.dr_lo |= rr << (8 * set); }
+            else { g.df_hi |= f << (8 * (set - 4)); g.dr_hi |= rr << (8 * (set - 4)); }
+        }
+        g.dx_lo = __vminu4(g.df_lo, g.dr_lo);
+        g.dx_hi = __vminu4(g.df_hi, g.dr_hi);
+        if (K == 3) {   // delay - dmin by new value and changed-pin set; value by pin values
+            for (int x = lane; x < 24; x += 32) {
+                const uint32_t F = (uint32_t)x >> 3, grp = (uint32_t)x & 7u;
+                sm.dtab[F][grp] = (uint8_t)(group_delay<3>(g, F, grp) - g.dmin);
+            }
+            for (int x = lane; x < 64; x += 32)
+                sm.f3[x] = (uint8_t)((((x & 32) ? g.lut_hi : g.lut_lo) >> (2 * (x & 31))) & 3u);
+            __syncwarp();
+        }
+        if (K == 2) {
+            const uint32_t l2 = (uint32_t)g.lut_hi;
+            for (int x = lane; x < 64; x += 32) {
+                const uint32_t F = (l2 >> (2 * (x & 15))) & 3u, grp = (uint32_t)x >> 4;
+                sm.ftab[x] = (uint16_t)(((group_delay<2>(g, F, grp) - g.dmin) << 2) | F);
+            }
+            __syncwarp();
+        }
+    } else {
+        for (int x = lane; x < 192; x += 32) {
+            const int F = x >> 6, vm = x & 63;
+            uint32_t d = 255u;
+            bool any = false;
+#pragma unroll
+            for (int p = 0; p < K; p++)
+#pragma unroll
+                for (int e = 0; e < 2; e++)
+                    if (((vm >> (2 * p + e)) & 1) && ((arcs >> p) & 1u)) {
+                        const uint32_t d0 = gr.doff[p][e][0], d1 = gr.doff[p][e][1];
+                        d = min(d, F == 0 ? d0 : (F == 1 ? d1 : min(d0, d1)));
+                        any = true;
+                    }
+            if (!any) d = F == 0 ? fb_f : (F == 1 ? fb_r : min(fb_f, fb_r));
+            sm.dtab[F][vm] = (uint8_t)d;
+        }
+        __syncwarp();
+    }
+}
+
+// Returns false only when a window copy did not complete within its poll
+// bound (the warp then stops: its buffers may still be written).
+template <int K, bool DEP, int CH, bool EDGE, bool MIRROR>
+__device__ bool eval_gate(const GateRec &gr, const RunDev &r, WarpSmem<CH> &sm, int lane, uint32_t &par,
+                          WarpArena &wa) {
+    GateCtx g;
+    uint64_t bound = 0;
+#pragma unroll
+    for (int p = 0; p < 3; p++) {
+        if (p < K) {
+            const int32_t n = gr.fin[p];
+            uint64_t ptr;
+            uint32_t len;
+            if (DEP) {  // written during this launch: read through L2
+                ptr = __ldcg(reinterpret_cast<const unsigned long long *>(r.net_ptr) + n);
+                len = __ldcg(r.net_len + n);
+            } else {
+                ptr = __ldg(reinterpret_cast<const unsigned long long *>(r.net_ptr) + n);
+                len = __ldg(r.net_len + n);
+            }
+            g.src[p] = reinterpret_cast<const uint32_t *>(ptr);
+            g.len[p] = len;
+        } else {
+            g.src[p] = nullptr;
+            g.len[p] = 0;
+        }
+        bound += g.len[p];
+    }
+    const uint32_t out_net = gr.out_net;
+
+    // state before the first input transition: pins at X, output X, nothing
+    // pending -- or, in a time slice, where the previous slice left the gate
+    uint32_t carry = 0x2Au;
+    CommitState cs{0u, kVX, 0};
+    uint32_t send = kTimeInf;   // transitions with t_r >= send stay pending
+    bool started = false;       // an input transition was evaluated (else the output is still at its X start)
+    if (r.st_in) {
+        const uint32_t h = r.st_in[out_net];
+        carry = (h & 63u) ^ 0x2Au;
+        started = (h >> 7) & 1u;
+        cs.lastV = ((h >> 8) & 3u) ^ kVX;
+        cs.np = (int)(h >> 16);
+        bound += (uint64_t)cs.np;   // each carried transition may become an output
+        send = r.slice_end;
+    }
+    if (bound == 0) {   // no input transition: the output stays as it is (X at the start, Algorithm 2)
+        if (lane == 0) {
+            r.net_ptr[out_net] = 0;
+            r.net_len[out_net] = 0;
+            if (r.st_in) r.st_out[out_net] = r.st_in[out_net];
+        }
+        return true;
+    }
+
+    // Claim the output slot and start the first window copies before the
+    // per-gate tables are built, so that the atomic's and the copies'
+    // latencies overlap that work.
+    const uint64_t need = (bound + kSlotAlign - 1) & ~(uint64_t)(kSlotAlign - 1);
+    const bool claim = wa.cur + need > wa.end;   // the same on every lane
+    const uint64_t blk = need > r.arena_blk ? need : (uint64_t)r.arena_blk;
+    unsigned long long base = 0;
+    if (claim && lane == 0) base = atomicAdd(r.arena_top, (unsigned long long)blk);
+    uint32_t cur[3] = {0, 0, 0};
+    bool failed = false;
+    const int b = 0;   // the one window buffer
+    int lead[3] = {0, 0, 0}, n[3] = {0, 0, 0};
+    __syncwarp();      // the previous gate's reads of the buffer precede the copies
+    bool more = issue_windows<K, CH>(sm, 0, g, cur, lead, n, lane);
+    const bool any_input = more;
+
+    build_tables<K, CH, EDGE>(gr, g, sm, lane);
+    if (claim) {
+        base = __shfl_sync(FULL, base, 0);
+        wa.end = base + blk;
+    } else {
+        base = wa.cur;
+    }
+    if (base + bound > r.arena_cap) {
+        wa.cur = wa.end = 0;   // past the arena: the next gate claims again (and counts its demand)
+        if (lane == 0) {
+            atomicOr(r.status, kStArenaOverflow);
+            r.net_ptr[out_net] = 0;
+            r.net_len[out_net] = 0;
+        }
+        // the copies already issued land in this warp's buffer: let them finish
+        if (more && !wait_window(sm, b, par)) {
+            if (lane == 0) atomicOr(r.status, kStTimeout);
+            return false;
+        }
+        return true;
+    }
+    uint32_t *out = r.arena + base;
+    uint32_t *hout = MIRROR ? r.harena + base : nullptr;
+    if (cs.np > 0) {   // carried transitions, moved to this slice's local time
+        const uint32_t *pp = r.pend_in + (size_t)out_net * PCAP;
+        for (int x = lane; x < cs.np; x += 32) sm.Q[x] = pp[x] - (r.slice_shift << 2);
+        __syncwarp();
+    }
+
+    if (!run_chunks<K, CH, EDGE, MIRROR>(r, sm, g, lane, par, more, cur, lead, n, carry, started, cs, send, out, hout,
+                                         failed))
+        return false;
     if (r.st_in && !failed) {
         // no input transition in this slice: settle the carried ones alone
         if (!any_input) failed = !commit_chunk<CH, MIRROR>(sm, lane, 0, 0, send, out, hout, cs);
