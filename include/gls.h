@@ -357,7 +357,9 @@ int gls_load_stimulus64(gls_ctx *ctx, int32_t n_pi, const int64_t *off, const in
 /*
  * Simulate netlist_id under stim_id (32- or 64-bit times) in time slices of
  * slice_ps picoseconds; synchronous: returns once every slice is evaluated and
- * copied to host memory.  The last slice runs to the end of all activity.
+ * copied to host memory (into the context's pinned host pool while it has
+ * room, GLS_OPT_HOST_POOL_BYTES).  The last slice runs to the end of all
+ * activity.
  * The windowed kernels only (GLS_EINVAL with GLS_KERNEL_SEGMENTED); either
  * schedule and a planned order apply.  arena_events sizes the event arena of
  * one launch (0: about 256 words per stimulus transition of the slices of a
@@ -366,7 +368,7 @@ int gls_load_stimulus64(gls_ctx *ctx, int32_t n_pi, const int64_t *off, const in
  * GLS_ERANGE when slice_ps + the longest path delay reaches 2^30 - 1, or when a
  * gate carries more than 256 scheduled transitions across a boundary;
  * GLS_EINVAL for more than 2^20 slices.  gls_run_stats reports the total
- * output transitions and the summed device time of the slices' gate kernels;
+ * output transitions and the summed device time of the launches' gate kernels;
  * gls_rerun evaluates every slice again (synchronously); gls_read_all,
  * gls_read_item and gls_read_waveform give GLS_EINVAL for sliced runs.
  */
